@@ -1,0 +1,292 @@
+"""Oracle: overlapping Schwarz smoothers with fast diagonalisation (Sec. 3.1).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Subdomains (Sec. 3.1, Fig. 2):
+  * element-centred (E): the element plus N_o node layers of each neighbour,
+    per axis N_P + 2 N_o nodes; the overlap in standard coordinates is
+    Delta xi_O = eta_{N_o} + 1.
+  * face-centred (F), normal direction d: the two half-elements adjoining the
+    face with the far-face node layers excluded (2 N_P - 2 nodes), laterally
+    like the element-centred case.
+
+Local problem (Eq. subproblem): A_ss = R_s A R_s^T inherits the tensor
+structure, so A_ss^{-1} = (S3 (x) S2 (x) S1) (sum of Lambda)^{-1} (...)^T with
+L_{s,d} S_d = M_{s,d} S_d Lambda_d, S_d^T M_{s,d} S_d = I (fast
+diagonalisation).  The generalised eigenproblem is solved with
+scipy.linalg.eigh.
+
+Weights (Eqs. weight function:ec, weight function:fc):
+  w_H(xi_H) = 1/2 [phi((1 + xi_H)/dxi_O) + phi((1 - xi_H)/dxi_O)],
+  phi = smoothed sign: phi~ on (-1, 1), sgn(x) for |x| >= 1,
+  phi~_3 = (3x - x^3)/2, phi~_5 = (15x - 10x^3 + 3x^5)/8,
+  unweighted: phi = 1; arithmetic: phi~ = 0.
+Readings:
+  C5  normal FA weight w_F = 1/2 [1 + phi(1 - |xi_F|)]: 1 at the face,
+      1/2 at element centres, 0 at the far faces (the printed
+      1/2 [1 + phi(|xi_F|)] is not a partition of unity).
+  C6  N_o = 0 (Delta xi_O = 0): tangential / element weights are 1.
+  C13 At a Dirichlet wall the face patch holds the wall element without its
+      far-face layer (N_P - 1 nodes normal); lateral overlap is truncated.
+  C18 At a Dirichlet wall the element-centred (and lateral) patch is
+      truncated and the transition term on the wall side of w_H is replaced by
+      its limit 1, which keeps the weights a partition of unity.
+  C11 Multiplicative ordering is lexicographic (x fastest).  EM keeps that
+      order in every sweep; FM reverses subdomain and sweep order in
+      post-smoothing (the symmetrisation of Sec. 3.1).  These are the variants
+      whose MG rates match Table 2 (EM: rows 1, 3; FM: row 15).
+  C12 FA sweeps run over directions 1..d in pre- AND post-smoothing (no
+      reversal): only this order reproduces the FA_0 rates of Tables 2, 3.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+from .dg import Discretisation
+
+
+# ----------------------------------------------------------------------------
+# transition functions and weights
+# ----------------------------------------------------------------------------
+
+def phi(x, kind):
+    """Smoothed sign function phi_i (Sec. 3.1)."""
+    x = np.asarray(x, dtype=np.float64)
+    if kind == "unweighted":
+        return np.ones_like(x)
+    if kind == "arithmetic":
+        inner = np.zeros_like(x)
+    elif kind == "cubic":
+        inner = (3 * x - x ** 3) / 2
+    elif kind == "quintic":
+        inner = (15 * x - 10 * x ** 3 + 3 * x ** 5) / 8
+    else:
+        raise ValueError(kind)
+    return np.where(np.abs(x) >= 1.0, np.sign(x), inner)
+
+
+def overlap_nodes(P_l: int, policy: str) -> int:
+    """Overlap N_o of level l (Sec. 4.3).
+
+    '0'  -> 0 (no overlap);
+    'l'  -> 1 + floor((P_l + 4) / 8), i.e. 1 + round(P_l / 8)   (reading C19);
+    'lf' -> 1 + floor(P_l / 8), the formula as printed.
+    The two differ only at P_l = 4 (2 vs 1 node layers).  The printed form does
+    not reproduce the paper's own EA_l rates at P = 4 (Tables 2, 3); the rounded
+    form does (see tests/test_oracle_mg.py).
+    """
+    if policy == "0":
+        return 0
+    if policy == "l":
+        return 1 + (P_l + 4) // 8
+    if policy == "lf":
+        return 1 + P_l // 8
+    raise ValueError(policy)
+
+
+class AxisPatch:
+    """One axis of one subdomain: global 1-D indices, weights, eigen-pairs."""
+
+    def __init__(self, idx, w, axis, mode="fdm"):
+        self.idx = np.asarray(idx, dtype=np.int64)
+        self.w = np.asarray(w, dtype=np.float64)
+        Ls = axis.L[self.idx][:, self.idx].toarray()
+        Ms = np.diag(axis.M[self.idx])
+        self.Ls, self.Ms = Ls, Ms
+        # generalised symmetric eigenproblem L S = M S Lambda, S^T M S = I
+        self.lam, self.S = sla.eigh(Ls, Ms)
+
+
+def ec_axis(axis, m, No, weighting):
+    """Element-centred patch of element m along one axis (Sec. 3.1)."""
+    P, NP, Ne, eta = axis.P, axis.NP, axis.Ne, axis.eta
+    idx, xi = [], []
+    has_left = axis.periodic or m > 0
+    has_right = axis.periodic or m < Ne - 1
+    if has_left:
+        ml = (m - 1) % Ne
+        for k in range(P - No + 1, P + 1):
+            idx.append(ml * NP + k)
+            xi.append(eta[k] - 2.0)
+    for i in range(NP):
+        idx.append(m * NP + i)
+        xi.append(eta[i])
+    if has_right:
+        mr = (m + 1) % Ne
+        for k in range(No):
+            idx.append(mr * NP + k)
+            xi.append(eta[k] + 2.0)
+    xi = np.asarray(xi)
+    if No == 0:
+        w = np.ones_like(xi)                                            # C6
+    else:
+        dxi = eta[No] + 1.0
+        left = phi((1 + xi) / dxi, weighting) if has_left else 1.0       # C18
+        right = phi((1 - xi) / dxi, weighting) if has_right else 1.0     # C18
+        w = 0.5 * (left + right)
+    return AxisPatch(idx, w, axis)
+
+
+def fc_axis(axis, f, weighting):
+    """Face-centred patch, normal direction, face f between elements f-1 and f (Sec. 3.1, C5, C13)."""
+    P, NP, Ne, eta = axis.P, axis.NP, axis.Ne, axis.eta
+    idx, xiF = [], []
+    if axis.periodic or f > 0:
+        ml = (f - 1) % Ne
+        for i in range(1, NP):
+            idx.append(ml * NP + i)
+            xiF.append(eta[i] - 1.0)
+    if axis.periodic or f < Ne:
+        mr = f % Ne
+        for i in range(0, NP - 1):
+            idx.append(mr * NP + i)
+            xiF.append(eta[i] + 1.0)
+    xiF = np.asarray(xiF)
+    w = 0.5 * (1.0 + phi(1.0 - np.abs(xiF), weighting))                 # C5
+    return AxisPatch(idx, w, axis)
+
+
+def n_faces(axis):
+    return axis.Ne if axis.periodic else axis.Ne + 1
+
+
+# ----------------------------------------------------------------------------
+# local solves
+# ----------------------------------------------------------------------------
+
+def fdm_solve(patches, rs):
+    """Fast diagonalisation A_ss^{-1} r_s (Sec. 3.1).  patches: per direction d (x first)."""
+    dim = len(patches)
+    t = rs
+    for d in range(dim):                       # S_d^T along direction d
+        t = np.moveaxis(np.tensordot(patches[d].S.T, np.moveaxis(t, dim - 1 - d, 0), axes=1), 0, dim - 1 - d)
+    lam = 0.0
+    for d in range(dim):
+        sh = [1] * dim
+        sh[dim - 1 - d] = -1
+        lam = lam + patches[d].lam.reshape(sh)
+    t = t / lam
+    for d in range(dim):                       # S_d along direction d
+        t = np.moveaxis(np.tensordot(patches[d].S, np.moveaxis(t, dim - 1 - d, 0), axes=1), 0, dim - 1 - d)
+    return t
+
+
+def dense_local_matrix(disc: Discretisation, patches):
+    """A_ss = R_s A R_s^T assembled densely from the tensor factors (Sec. 3.1)."""
+    dim = disc.dim
+    terms = []
+    for d in range(dim):
+        fac = [patches[e].Ls if e == d else patches[e].Ms for e in range(dim)]
+        K = fac[dim - 1]
+        for e in range(dim - 2, -1, -1):
+            K = np.kron(K, fac[e])
+        terms.append(K)
+    return sum(terms)
+
+
+def weight_tensor(patches):
+    dim = len(patches)
+    w = patches[dim - 1].w
+    for d in range(dim - 2, -1, -1):
+        w = np.multiply.outer(w, patches[d].w)
+    return w
+
+
+def _ix(patches):
+    return np.ix_(*[p.idx for p in reversed(patches)])
+
+
+# ----------------------------------------------------------------------------
+# smoothers
+# ----------------------------------------------------------------------------
+
+class Smoother:
+    """Schwarz smoother for one level.
+
+    kind: 'EA' | 'FA' | 'EM' | 'FM'  (Sec. 4.3 acronyms)
+    overlap: '0' | 'l';  weighting: 'unweighted' | 'arithmetic' | 'cubic' | 'quintic'
+    omega: damping of the additive update (1 in the paper; reading C15).
+    """
+
+    def __init__(self, disc: Discretisation, kind="EA", overlap="l", weighting="quintic", omega=1.0,
+                 symmetrize=None):
+        self.disc = disc
+        self.kind = kind
+        # reading C11: FM symmetrised, EM not
+        self.symmetrize = (kind == "FM") if symmetrize is None else bool(symmetrize)
+        self.No = overlap_nodes(disc.P, overlap)
+        self.weighting = weighting
+        self.omega = omega
+        dim = disc.dim
+        self.ec = [[ec_axis(disc.axes[d], m, self.No, weighting) for m in range(disc.axes[d].Ne)]
+                   for d in range(dim)]
+        if kind in ("FA", "FM"):
+            self.fc = [[fc_axis(disc.axes[d], f, weighting) for f in range(n_faces(disc.axes[d]))]
+                       for d in range(dim)]
+
+    # -- subdomain enumeration (lexicographic: x fastest) ----------------
+    def subdomains(self, normal=None):
+        """List of per-direction AxisPatch tuples; normal=None -> element-centred."""
+        dim = self.disc.dim
+        counts = []
+        for d in range(dim):
+            if normal is not None and d == normal:
+                counts.append(len(self.fc[d]))
+            else:
+                counts.append(len(self.ec[d]))
+        out = []
+        for flat in range(int(np.prod(counts))):
+            ids = []
+            rem = flat
+            for d in range(dim):
+                ids.append(rem % counts[d])
+                rem //= counts[d]
+            out.append(tuple((self.fc[d][ids[d]] if (normal is not None and d == normal)
+                              else self.ec[d][ids[d]]) for d in range(dim)))
+        return out
+
+    def additive_sweep(self, U, F, normal=None):
+        """u += omega sum_s R_s^T (w A_ss^{-1} R_s (f - A u))  (Eq. correction:global)."""
+        R = F - self.disc.apply(U)
+        dU = np.zeros_like(U)
+        for pt in self.subdomains(normal):
+            ix = _ix(pt)
+            ds = fdm_solve(pt, R[ix])
+            np.add.at(dU, ix, weight_tensor(pt) * ds)
+        return U + self.omega * dU
+
+    def multiplicative_sweep(self, U, F, normal=None, reverse=False):
+        """Sequential subdomain solves with the residual recomputed each time (Sec. 3.1)."""
+        subs = self.subdomains(normal)
+        if reverse:
+            subs = subs[::-1]
+        U = U.copy()
+        for pt in subs:
+            ix = _ix(pt)
+            R = F - self.disc.apply(U)
+            U[ix] += fdm_solve(pt, R[ix])
+        return U
+
+    def step(self, U, F, post=False):
+        """One Schwarz iteration.  FA/FM: one sweep per direction (C11, C12 order)."""
+        dim = self.disc.dim
+        rev = post and self.symmetrize
+        if self.kind == "EA":
+            return self.additive_sweep(U, F)
+        if self.kind == "EM":
+            return self.multiplicative_sweep(U, F, reverse=rev)
+        order = list(range(dim))
+        if rev:
+            order = order[::-1]
+        for d in order:
+            if self.kind == "FA":
+                U = self.additive_sweep(U, F, normal=d)
+            else:
+                U = self.multiplicative_sweep(U, F, normal=d, reverse=rev)
+        return U
+
+    def smooth(self, U, F, nsteps, post=False):
+        for _ in range(nsteps):
+            U = self.step(U, F, post=post)
+        return U
