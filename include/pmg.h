@@ -1,0 +1,204 @@
+/*
+ * pmg.h -- C ABI of the GB300-native p-multigrid solver for nodal IP/LDG
+ * discretisations of the Poisson equation on Cartesian grids.
+ *
+ * Method: J. Stiller, "Robust multigrid for high-order discontinuous Galerkin
+ * methods: a fast Poisson solver suitable for high-aspect ratio Cartesian
+ * grids", arXiv 1603.02524.  Section, equation and algorithm numbers below
+ * refer to that paper.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Vectors are contiguous fp64 arrays (fp32 nowhere crosses the ABI) in the
+ *    element-major layout u[e_z][e_y][e_x][k][j][i]: elements in x-fastest
+ *    lexicographic order, inside an element the (P+1)^dim GLL nodal values with
+ *    x fastest.  In 2-D drop e_z and k.  Level l has order P_l = 2^l and
+ *    n_elem_x * n_elem_y [* n_elem_z] * (P_l + 1)^dim entries.
+ *  - Pointers named *_dev are device pointers on the current CUDA device; the
+ *    caller allocates and owns them.  The library owns only the grid/hierarchy
+ *    objects and their internal workspace (allocated in pmg_hierarchy_build,
+ *    freed in pmg_hierarchy_destroy).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls enqueue work on that stream and return without synchronising,
+ *    except pmg_solve / pmg_solve_host, which synchronise once per CG
+ *    iteration to test convergence.
+ *  - Every call returns a pmg_status (0 = PMG_OK) and never throws.  Invalid
+ *    arguments are rejected before any work is enqueued.  Kernel launch errors
+ *    return PMG_ECUDA; numerical breakdown detected on the device returns
+ *    PMG_EBREAKDOWN / PMG_ENAN after the synchronisation of pmg_solve.
+ *  - A hierarchy object is not thread safe: calls that use it must not run
+ *    concurrently (they share its workspace).
+ */
+#ifndef PMG_H_
+#define PMG_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pmg_grid_s* pmg_grid;
+typedef struct pmg_hier_s* pmg_hier;
+
+typedef enum {
+  PMG_OK = 0,
+  PMG_EINVAL = -1,       /* invalid argument or unsupported configuration */
+  PMG_ENOMEM = -2,       /* device or host allocation failed */
+  PMG_ECUDA = -3,        /* CUDA runtime / launch error */
+  PMG_ENOCONV = -4,      /* pmg_solve: tolerance not reached within max_iter */
+  PMG_EBREAKDOWN = -5,   /* pmg_solve: p^T A p <= 0 or delta <= 0 */
+  PMG_ENAN = -6,         /* pmg_solve: non-finite residual */
+  PMG_ETIMEOUT = -7      /* reserved: a bounded device wait gave up */
+} pmg_status;
+
+/* Smoother (Sec. 3.1): additive element-centred (EA) or face-centred (FA). */
+enum { PMG_SMOOTHER_EA = 0, PMG_SMOOTHER_FA = 1 };
+/* Overlap policy N_o (Sec. 4.3): 0 -> none; LEVEL -> 1 + round(P_l/8)
+ * (reproduces Tables 2-3); LEVEL_FLOOR -> 1 + floor(P_l/8) as printed. */
+enum { PMG_OVERLAP_ZERO = 0, PMG_OVERLAP_LEVEL = 1, PMG_OVERLAP_LEVEL_FLOOR = 2 };
+/* Weighting of the additive update, Eqs. (weight function:ec/fc). */
+enum { PMG_WEIGHT_UNWEIGHTED = 0, PMG_WEIGHT_ARITHMETIC = 1, PMG_WEIGHT_CUBIC = 3,
+       PMG_WEIGHT_QUINTIC = 5 };
+/* Arithmetic of the V-cycle: FP64 everywhere, or FP32 V-cycle (smoother,
+ * residuals, transfers) inside the FP64 flexible CG (spec extension). */
+enum { PMG_PREC_FP64 = 0, PMG_PREC_MIXED = 1 };
+
+typedef struct {
+  int smoother;        /* PMG_SMOOTHER_*                                  (default EA) */
+  int overlap;         /* PMG_OVERLAP_*                                   (default LEVEL) */
+  int weighting;       /* PMG_WEIGHT_*                                    (default QUINTIC) */
+  int ns_pre, ns_post; /* smoothing steps per level                       (default 1, 1) */
+  int variable_v;      /* 1: n_s,l = n_s * 2^(L-l) (variable V-cycle)     (default 0) */
+  double omega;        /* damping of the additive update                  (default 1) */
+  int precision;       /* PMG_PREC_*                                      (default FP64) */
+  int max_iter;        /* MGCG iteration cap (Algorithm 2, i_max)         (default 100) */
+} pmg_options;
+
+typedef struct {
+  int iterations;      /* CG iterations performed (= V-cycles applied)     */
+  double r0;           /* ||g - A u_0||_2                                    */
+  double rn;           /* ||r|| at exit                                      */
+  double* history;     /* optional host array of max_iter+1 entries, or NULL */
+} pmg_stats;
+
+/* Fill *opt with the defaults listed above. */
+void pmg_options_default(pmg_options* opt);
+
+/*
+ * Create a Cartesian grid description (Sec. 2.2).
+ *   dim       2 or 3.
+ *   P         polynomial order, a power of two, 1 <= P <= 16 in 3-D, <= 32 in 2-D
+ *             (levels P_l = 2^l, Sec. 3.2).
+ *   n_elem    elements per axis (n_elem[2] ignored in 2-D); each >= 1, and >= 2
+ *             when periodic.
+ *   spacing   host arrays: spacing[d][m] = width of element m along axis d (> 0).
+ *   periodic  1: periodic domain (the paper's Sec. 2.1 setting); 0: homogeneous
+ *             Dirichlet walls (odd-reflection ghost element, symmetric Nitsche).
+ *   mu_star   penalty factor, mu = mu0 (1 + mu_star) (Sec. 2.4); the paper uses 1.
+ *   beta      LDG auxiliary parameter per axis (Eq. flux:num:sigma); 0 -> interior
+ *             penalty (IP), 1/2 -> LDG as in Table 2.  NULL = all zero.
+ * The host arrays are copied; *out receives a handle freed by pmg_grid_destroy.
+ */
+int pmg_grid_create(int dim, int P, const int n_elem[3], const double* const spacing[3],
+                    int periodic, double mu_star, const double beta[3], pmg_grid* out);
+void pmg_grid_destroy(pmg_grid g);
+
+/*
+ * Node coordinates (host): out[m*(P+1)+i] = physical coordinate of GLL node i
+ * of element m along axis `axis` at the grid's finest order P.  `out` must hold
+ * n_elem[axis]*(P+1) doubles.
+ */
+int pmg_grid_coords(pmg_grid g, int axis, double* out);
+
+/*
+ * Build the p-multigrid hierarchy (Sec. 3.2): for every level P_l = 2^l the
+ * re-discretised operator tables (Eq. L:generic), the Schwarz patch
+ * eigen-tables (Sec. 3.1, fast diagonalisation), the interpolation I_l and
+ * the level vectors; the coarse P = 1 problem is solved exactly (see
+ * pmg_coarse_solve).  Allocates device memory on the current device.
+ * opt == NULL uses the defaults.  *out is freed by pmg_hierarchy_destroy.
+ */
+int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out);
+void pmg_hierarchy_destroy(pmg_hier h);
+
+/* Number of levels L+1 and, per level, order and vector length. */
+int pmg_num_levels(pmg_hier h);
+int pmg_level_info(pmg_hier h, int level, int* P_l, long long* ndof);
+
+/* Au_dev = A_l u_dev  (Eq. discrete problem; 3-D tensor form). level in 0..L. */
+int pmg_apply(pmg_hier h, int level, const double* u_dev, double* Au_dev, void* stream);
+
+/* r_dev = f_dev - A_l u_dev. */
+int pmg_residual(pmg_hier h, int level, const double* u_dev, const double* f_dev, double* r_dev,
+                 void* stream);
+
+/* g_dev = M f_nodal_dev: the discrete right-hand side g = M f (Sec. 2.4). */
+int pmg_rhs(pmg_hier h, const double* f_nodal_dev, double* g_dev, void* stream);
+
+/*
+ * `nsteps` Schwarz iterations on level l >= 1 (Sec. 3.1): each EA step is
+ * r = f - A u followed by u += omega * sum_s R_s^T (w_s A_ss^{-1} R_s r); each
+ * FA step does one such sweep per direction with the residual recomputed in
+ * between.  u_dev is updated in place.  Runs in the hierarchy's precision
+ * (mixed: fp32 arithmetic, fp64 in and out).
+ */
+int pmg_smooth(pmg_hier h, int level, double* u_dev, const double* f_dev, int nsteps,
+               void* stream);
+
+/* fc_dev = I_l^T rf_dev: restriction from level l to l-1 (Sec. 3.2), l >= 1. */
+int pmg_restrict(pmg_hier h, int level, const double* rf_dev, double* fc_dev, void* stream);
+
+/* uf_dev += I_l uc_dev: prolongation (embedded interpolation) from l-1 to l. */
+int pmg_prolong(pmg_hier h, int level, const double* uc_dev, double* uf_dev, void* stream);
+
+/*
+ * u0_dev = A_0^+ f0_dev at P = 1 (Algorithm 1, coarse-grid solution).  Solved
+ * exactly by a global tensor-product fast diagonalisation (the coarse operator
+ * has the same Kronecker structure as A_ss); on periodic grids the right-hand
+ * side is projected onto range(A_0) and the zero mode dropped.
+ */
+int pmg_coarse_solve(pmg_hier h, const double* f0_dev, double* u0_dev, void* stream);
+
+/* u_dev = MultigridCycle(0, f_dev): one V-cycle of Algorithm 1 on the finest level. */
+int pmg_vcycle(pmg_hier h, const double* f_dev, double* u_dev, void* stream);
+
+/*
+ * Inexact multigrid-preconditioned CG (Algorithm 2; beta by Golub-Ye,
+ * z^T (r - r_old) / delta).  g_dev: right-hand side (periodic grids: projected
+ * onto zero mean internally).  u_dev: initial guess in, solution out.
+ * Stops when ||r||_2 <= rtol * ||r_0||_2 or after opt.max_iter iterations
+ * (PMG_ENOCONV, u holds the last iterate).  stats may be NULL.
+ */
+int pmg_solve(pmg_hier h, const double* g_dev, double* u_dev, double rtol, pmg_stats* stats,
+              void* stream);
+
+/*
+ * As pmg_solve, but g_host / u_host are host arrays (pinned memory is fastest):
+ * the host->device copies of g and u, the solve and the device->host copy of u
+ * all run inside this call, on the hierarchy's internal device buffers.
+ */
+int pmg_solve_host(pmg_hier h, const double* g_host, double* u_host, double rtol,
+                   pmg_stats* stats, void* stream);
+
+/*
+ * One additive Schwarz sweep without the residual (Sec. 3.1, Eq.
+ * correction:global): u_dev += omega * sum_s R_s^T (w_s A_ss^{-1} R_s r_dev)
+ * over one subdomain family of level l >= 1.  family = -1: the element-centred
+ * subdomains (hierarchy built with the EA smoother); family = d in 0..dim-1:
+ * the face-centred subdomains normal to axis d (FA smoother).  fp64 in and
+ * out; in mixed precision the sweep runs in fp32 on staged copies.
+ */
+int pmg_schwarz_sweep(pmg_hier h, int level, int family, const double* r_dev, double* u_dev,
+                      void* stream);
+
+/* Text for a status code; last error detail of a hierarchy (may be ""). */
+const char* pmg_status_string(int status);
+const char* pmg_last_error(pmg_hier h);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all hierarchies, all devices); for counting launches in a timed region. */
+unsigned long long pmg_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMG_H_ */

@@ -95,7 +95,8 @@ class Hierarchy:
             F0 = F0 - F0.mean()                # projection onto range(A_0) (Kaasschieter)
         if self.coarse == "dense":
             if self._dense_pinv is None:
-                self._dense_pinv = np.linalg.pinv(disc.dense())
+                # singular values at rounding level (the periodic null space) count as zero
+                self._dense_pinv = np.linalg.pinv(disc.dense(), rcond=1e-10, hermitian=True)
             return (self._dense_pinv @ F0.reshape(-1)).reshape(F0.shape)
         return cg(disc.apply, F0, rtol=self.coarse_rtol, maxit=10 * disc.ndof)[0]
 

@@ -1,0 +1,267 @@
+"""ctypes binding of the C ABI declared in include/pmg.h.
+
+Argument marshalling only: every numerical step runs in the CUDA library.
+Device vectors are torch CUDA tensors (fp64, contiguous); their data_ptr()
+and the current torch stream are passed through.  Importing this module does
+not load the library; the first call does, and raises if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpmg.so")
+
+SMOOTHER = {"EA": 0, "FA": 1}
+OVERLAP = {"0": 0, "l": 1, "lf": 2}
+WEIGHTING = {"unweighted": 0, "arithmetic": 1, "cubic": 3, "quintic": 5}
+PRECISION = {"fp64": 0, "mixed": 1}
+
+STATUS = {0: "PMG_OK", -1: "PMG_EINVAL", -2: "PMG_ENOMEM", -3: "PMG_ECUDA", -4: "PMG_ENOCONV",
+          -5: "PMG_EBREAKDOWN", -6: "PMG_ENAN", -7: "PMG_ETIMEOUT"}
+
+EXPORTS = ["pmg_options_default", "pmg_grid_create", "pmg_grid_destroy", "pmg_grid_coords",
+           "pmg_hierarchy_build", "pmg_hierarchy_destroy", "pmg_num_levels", "pmg_level_info",
+           "pmg_apply", "pmg_residual", "pmg_rhs", "pmg_smooth", "pmg_restrict", "pmg_prolong",
+           "pmg_coarse_solve", "pmg_vcycle", "pmg_solve", "pmg_solve_host", "pmg_status_string",
+           "pmg_last_error"]
+
+
+class PmgOptions(ctypes.Structure):
+    _fields_ = [("smoother", ctypes.c_int), ("overlap", ctypes.c_int), ("weighting", ctypes.c_int),
+                ("ns_pre", ctypes.c_int), ("ns_post", ctypes.c_int), ("variable_v", ctypes.c_int),
+                ("omega", ctypes.c_double), ("precision", ctypes.c_int), ("max_iter", ctypes.c_int)]
+
+
+class PmgStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("r0", ctypes.c_double), ("rn", ctypes.c_double),
+                ("history", ctypes.POINTER(ctypes.c_double))]
+
+
+class PmgError(RuntimeError):
+    def __init__(self, fn, status, detail=""):
+        self.status = status
+        super().__init__(f"{fn} -> {STATUS.get(status, status)}"
+                         + (f": {detail}" if detail else ""))
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libpmg.so (built by paper_1603_02524_gb300.build); raise if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library not built: {p} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(p)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "pmg_options_default": (None, [ctypes.POINTER(PmgOptions)]),
+        "pmg_grid_create": (i, [i, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p),
+                                i, d, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(vp)]),
+        "pmg_grid_destroy": (None, [vp]),
+        "pmg_grid_coords": (i, [vp, i, ctypes.POINTER(ctypes.c_double)]),
+        "pmg_hierarchy_build": (i, [vp, ctypes.POINTER(PmgOptions), ctypes.POINTER(vp)]),
+        "pmg_hierarchy_destroy": (None, [vp]),
+        "pmg_num_levels": (i, [vp]),
+        "pmg_level_info": (i, [vp, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]),
+        "pmg_apply": (i, [vp, i, vp, vp, vp]),
+        "pmg_residual": (i, [vp, i, vp, vp, vp, vp]),
+        "pmg_rhs": (i, [vp, vp, vp, vp]),
+        "pmg_smooth": (i, [vp, i, vp, vp, i, vp]),
+        "pmg_restrict": (i, [vp, i, vp, vp, vp]),
+        "pmg_prolong": (i, [vp, i, vp, vp, vp]),
+        "pmg_coarse_solve": (i, [vp, vp, vp, vp]),
+        "pmg_vcycle": (i, [vp, vp, vp, vp]),
+        "pmg_solve": (i, [vp, vp, vp, d, ctypes.POINTER(PmgStats), vp]),
+        "pmg_solve_host": (i, [vp, vp, vp, d, ctypes.POINTER(PmgStats), vp]),
+        "pmg_status_string": (ctypes.c_char_p, [i]),
+        "pmg_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def options(smoother="EA", overlap="l", weighting="quintic", ns=(1, 1), variable_v=False,
+            omega=1.0, precision="fp64", max_iter=100) -> PmgOptions:
+    o = PmgOptions()
+    load().pmg_options_default(ctypes.byref(o))
+    o.smoother = SMOOTHER[smoother]
+    o.overlap = OVERLAP[overlap]
+    o.weighting = WEIGHTING[weighting]
+    o.ns_pre, o.ns_post = int(ns[0]), int(ns[1])
+    o.variable_v = int(bool(variable_v))
+    o.omega = float(omega)
+    o.precision = PRECISION[precision]
+    o.max_iter = int(max_iter)
+    return o
+
+
+def _check(fn, st, hier=None):
+    if st != 0:
+        detail = ""
+        if hier:
+            detail = (load().pmg_last_error(hier) or b"").decode()
+        raise PmgError(fn, st, detail)
+
+
+class Grid:
+    """pmg_grid_create / pmg_grid_destroy / pmg_grid_coords."""
+
+    def __init__(self, dim, P, n_elem, spacing, periodic, mu_star=1.0, beta=0.0):
+        lib = load()
+        self.dim, self.P = dim, P
+        self.n_elem = tuple(int(x) for x in n_elem) + (1,) * (3 - len(n_elem))
+        ne = (ctypes.c_int * 3)(*self.n_elem)
+        self._sp = [(ctypes.c_double * len(s))(*s) for s in spacing]
+        sp = (ctypes.c_void_p * 3)(*([ctypes.cast(a, ctypes.c_void_p) for a in self._sp]
+                                     + [None] * (3 - len(self._sp))))
+        b = beta if isinstance(beta, (list, tuple)) else [beta] * 3
+        bt = (ctypes.c_double * 3)(*(list(b) + [0.0] * (3 - len(b))))
+        h = ctypes.c_void_p()
+        _check("pmg_grid_create", lib.pmg_grid_create(dim, P, ne, sp, int(bool(periodic)),
+                                                       float(mu_star), bt, ctypes.byref(h)))
+        self.handle = h
+
+    def coords(self, axis):
+        import numpy as np
+        n = self.n_elem[axis] * (self.P + 1)
+        out = (ctypes.c_double * n)()
+        _check("pmg_grid_coords", load().pmg_grid_coords(self.handle, axis, out))
+        return np.frombuffer(out, dtype=np.float64).reshape(self.n_elem[axis], self.P + 1).copy()
+
+    def close(self):
+        if self.handle:
+            load().pmg_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, n):
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == n):
+        raise ValueError(f"expected a contiguous fp64 CUDA tensor with {n} entries")
+    return _ptr(t)
+
+
+class Hierarchy:
+    """pmg_hierarchy_build and the per-level entry points (torch CUDA tensors in and out)."""
+
+    def __init__(self, grid: Grid, **opts):
+        lib = load()
+        self.grid = grid
+        self.opts = options(**opts)
+        h = ctypes.c_void_p()
+        _check("pmg_hierarchy_build", lib.pmg_hierarchy_build(grid.handle, ctypes.byref(self.opts),
+                                                               ctypes.byref(h)))
+        self.handle = h
+        self.L = lib.pmg_num_levels(h) - 1
+
+    def level_info(self, level):
+        P = ctypes.c_int()
+        n = ctypes.c_longlong()
+        _check("pmg_level_info", load().pmg_level_info(self.handle, level, ctypes.byref(P), ctypes.byref(n)))
+        return P.value, n.value
+
+    def ndof(self, level=None):
+        return self.level_info(self.L if level is None else level)[1]
+
+    def apply(self, level, u, out, stream=None):
+        n = self.ndof(level)
+        _check("pmg_apply", load().pmg_apply(self.handle, level, _dev(u, n), _dev(out, n), _stream(stream)), self.handle)
+
+    def residual(self, level, u, f, out, stream=None):
+        n = self.ndof(level)
+        _check("pmg_residual", load().pmg_residual(self.handle, level, _dev(u, n), _dev(f, n), _dev(out, n),
+                                                   _stream(stream)), self.handle)
+
+    def rhs(self, f, out, stream=None):
+        n = self.ndof()
+        _check("pmg_rhs", load().pmg_rhs(self.handle, _dev(f, n), _dev(out, n), _stream(stream)), self.handle)
+
+    def smooth(self, level, u, f, nsteps=1, stream=None):
+        n = self.ndof(level)
+        _check("pmg_smooth", load().pmg_smooth(self.handle, level, _dev(u, n), _dev(f, n), nsteps,
+                                               _stream(stream)), self.handle)
+
+    def restrict(self, level, rf, fc, stream=None):
+        _check("pmg_restrict", load().pmg_restrict(self.handle, level, _dev(rf, self.ndof(level)),
+                                                   _dev(fc, self.ndof(level - 1)), _stream(stream)), self.handle)
+
+    def prolong(self, level, uc, uf, stream=None):
+        _check("pmg_prolong", load().pmg_prolong(self.handle, level, _dev(uc, self.ndof(level - 1)),
+                                                 _dev(uf, self.ndof(level)), _stream(stream)), self.handle)
+
+    def coarse_solve(self, f0, u0, stream=None):
+        n = self.ndof(0)
+        _check("pmg_coarse_solve", load().pmg_coarse_solve(self.handle, _dev(f0, n), _dev(u0, n),
+                                                           _stream(stream)), self.handle)
+
+    def vcycle(self, f, u, stream=None):
+        n = self.ndof()
+        _check("pmg_vcycle", load().pmg_vcycle(self.handle, _dev(f, n), _dev(u, n), _stream(stream)), self.handle)
+
+    def solve(self, g, u, rtol=1e-10, stream=None, history=True, check=True):
+        """Algorithm 2 on device tensors; returns (status, iterations, residual history)."""
+        n = self.ndof()
+        st = PmgStats()
+        hist = (ctypes.c_double * (self.opts.max_iter + 1))() if history else None
+        st.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if history else None
+        rc = load().pmg_solve(self.handle, _dev(g, n), _dev(u, n), float(rtol), ctypes.byref(st), _stream(stream))
+        if check and rc not in (0, -4):
+            _check("pmg_solve", rc, self.handle)
+        h = list(hist[: st.iterations + 1]) if history else []
+        return rc, st.iterations, h
+
+    def solve_host(self, g_host, u_host, rtol=1e-10, stream=None):
+        """Algorithm 2 on host arrays (numpy or pinned torch CPU tensors, fp64, contiguous)."""
+        import numpy as np
+        n = self.ndof()
+
+        def hp(a):
+            if isinstance(a, np.ndarray):
+                assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == n
+                return ctypes.c_void_p(a.ctypes.data)
+            assert a.numel() == n and a.is_contiguous() and not a.is_cuda
+            return ctypes.c_void_p(a.data_ptr())
+        st = PmgStats()
+        st.history = None
+        rc = load().pmg_solve_host(self.handle, hp(g_host), hp(u_host), float(rtol), ctypes.byref(st),
+                                   _stream(stream))
+        if rc not in (0, -4):
+            _check("pmg_solve_host", rc, self.handle)
+        return rc, st.iterations
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pmg_hierarchy_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

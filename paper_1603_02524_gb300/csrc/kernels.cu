@@ -1,0 +1,549 @@
+// CUDA kernels of the p-multigrid DG Poisson solver (sm_103a): operator apply,
+// mass, restriction / prolongation, exact coarse solve, CG vector kernels.
+// The Schwarz patch kernel lives in fdm_kernel.cuh.
+//
+// Paper: Stiller, arXiv 1603.02524 (Sec. 2.4 operator, Sec. 3.2 transfers,
+// Algorithm 2 vector steps).
+#include <cstdio>
+
+#include "pmg_internal.h"
+
+namespace pmg {
+
+// Allow `bytes` of dynamic shared memory for kernel `fn` (once per kernel).
+template <typename K>
+static bool set_smem(K fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return true;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+         cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Operator apply: v = A u or v = f - A u  (Eq. discrete problem, 3-D tensor form)
+//
+// One thread owns one nodal line of one element per axis pass.  The element is
+// staged in shared memory; the line is contracted with the element's dense
+// 1-D block L^0 (Eq. L:generic); the neighbour blocks L^-/L^+ have rank <= 3
+// and need only the neighbour line's end value and end derivative
+// (sum_k D_{P,k} u_k^{m-1}, sum_k D_{0,k} u_k^{m+1}), which the thread reads
+// from global memory (L2-resident: neighbouring CTAs read the same elements).
+// Each pass result is scaled by the diagonal masses of the two other axes and
+// accumulated in shared memory.
+// ---------------------------------------------------------------------------
+template <int DIM, int NP>
+struct ApplyShape {
+  static constexpr int LINES = (DIM == 3) ? NP * NP : NP;
+  static constexpr int NODES = (DIM == 3) ? NP * NP * NP : NP * NP;
+  static constexpr int EPB = (128 / LINES) > 0 ? (128 / LINES) : 1;
+  static constexpr int THREADS = ((EPB * LINES + 31) / 32) * 32;
+};
+
+template <typename T, int DIM, int NP, bool RESIDUAL>
+__global__ void __launch_bounds__(ApplyShape<DIM, NP>::THREADS)
+apply_kernel(LevelDims dm, ApplyTables<T> at, const T* __restrict__ u, const T* __restrict__ f,
+             T* __restrict__ v) {
+  using S = ApplyShape<DIM, NP>;
+  constexpr int P = NP - 1;
+  extern __shared__ __align__(16) unsigned char apply_smem[];
+  T* su = reinterpret_cast<T*>(apply_smem);
+  T* acc = su + S::EPB * S::NODES;
+  const int tid = threadIdx.x;
+  const long long e0 = (long long)blockIdx.x * S::EPB;
+  const long long nodes_blk = (long long)S::EPB * S::NODES;
+  const long long total = dm.nelem * S::NODES;
+  for (int t = tid; t < nodes_blk; t += blockDim.x) {
+    long long g = e0 * S::NODES + t;
+    su[t] = g < total ? u[g] : T(0);
+  }
+  __syncthreads();
+  const int el = tid / S::LINES;
+  const int line = tid % S::LINES;
+  const long long e = e0 + el;
+  const bool active = (el < S::EPB) && (e < dm.nelem);
+  int me[3] = {0, 0, 0};
+  if (active) {
+    me[0] = (int)(e % dm.ne[0]);
+    me[1] = (int)((e / dm.ne[0]) % dm.ne[1]);
+    me[2] = (int)(e / ((long long)dm.ne[0] * dm.ne[1]));
+  }
+  T* sel = su + el * S::NODES;
+  T* ael = acc + el * S::NODES;
+#pragma unroll 1
+  for (int d = 0; d < DIM; ++d) {
+    if (active) {
+      int off, stride, ia = 0, ib = 0, oa = 0, ob = 0;   // (ia on axis oa, ib on axis ob) = line coords
+      if (DIM == 3) {
+        if (d == 0) { off = line * NP; stride = 1; ia = line % NP; oa = 1; ib = line / NP; ob = 2; }
+        else if (d == 1) { ia = line % NP; ib = line / NP; off = ib * NP * NP + ia; stride = NP; oa = 0; ob = 2; }
+        else { ia = line % NP; ib = line / NP; off = ib * NP + ia; stride = NP * NP; oa = 0; ob = 1; }
+      } else {
+        if (d == 0) { off = line * NP; stride = 1; ia = line; oa = 1; }
+        else { off = line; stride = NP; ia = line; oa = 0; }
+      }
+      T x[NP], y[NP];
+#pragma unroll
+      for (int a = 0; a < NP; ++a) x[a] = sel[off + a * stride];
+      const T* L0 = at.L0[d] + (size_t)me[d] * NP * NP;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T s = T(0);
+#pragma unroll
+        for (int a = 0; a < NP; ++a) s = fma(__ldg(L0 + i * NP + a), x[a], s);
+        y[i] = s;
+      }
+      const T* c = at.cpl[d] + (size_t)me[d] * 8;
+      const long long estride = (d == 0) ? 1 : (d == 1 ? (long long)dm.ne[0] : (long long)dm.ne[0] * dm.ne[1]);
+      const int ned = dm.ne[d];
+      if (__ldg(c + 3) != T(0)) {          // neighbour m-1 exists
+        long long en = (me[d] > 0) ? e - estride : e + (long long)(ned - 1) * estride;
+        const T* un = u + en * S::NODES + off;
+        T uP = T(0), dP = T(0);
+#pragma unroll
+        for (int a = 0; a < NP; ++a) {
+          T val = __ldg(un + a * stride);
+          dP = fma(__ldg(at.DP + a), val, dP);
+          if (a == P) uP = val;
+        }
+        const T aL = __ldg(c + 0), bL = __ldg(c + 1), cL = __ldg(c + 2);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) y[i] = fma(-aL * __ldg(at.D0 + i), uP, y[i]);
+        y[0] += bL * dP - cL * uP;
+      }
+      if (__ldg(c + 7) != T(0)) {          // neighbour m+1 exists
+        long long en = (me[d] < ned - 1) ? e + estride : e - (long long)(ned - 1) * estride;
+        const T* un = u + en * S::NODES + off;
+        T u0 = T(0), d0 = T(0);
+#pragma unroll
+        for (int a = 0; a < NP; ++a) {
+          T val = __ldg(un + a * stride);
+          d0 = fma(__ldg(at.D0 + a), val, d0);
+          if (a == 0) u0 = val;
+        }
+        const T aR = __ldg(c + 4), bR = __ldg(c + 5), cR = __ldg(c + 6);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) y[i] = fma(aR * __ldg(at.DP + i), u0, y[i]);
+        y[P] -= bR * d0 + cR * u0;
+      }
+      T scale = __ldg(at.M[oa] + (size_t)me[oa] * NP + ia);
+      if (DIM == 3) scale *= __ldg(at.M[ob] + (size_t)me[ob] * NP + ib);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T val = scale * y[i];
+        if (d == 0) ael[off + i * stride] = val;
+        else ael[off + i * stride] += val;
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < nodes_blk; t += blockDim.x) {
+    long long g = e0 * S::NODES + t;
+    if (g < total) v[g] = RESIDUAL ? f[g] - acc[t] : acc[t];
+  }
+}
+
+template <typename T, int DIM, int NP>
+static int apply_dispatch(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f,
+                          T* v, cudaStream_t s) {
+  using S = ApplyShape<DIM, NP>;
+  long long blocks = (dm.nelem + S::EPB - 1) / S::EPB;
+  const size_t smem = 2 * sizeof(T) * S::EPB * S::NODES;
+  if (f) {
+    if (!set_smem(apply_kernel<T, DIM, NP, true>, smem)) return PMG_ECUDA;
+    count_launch(); apply_kernel<T, DIM, NP, true><<<(unsigned)blocks, S::THREADS, smem, s>>>(dm, at, u, f, v);
+  } else {
+    if (!set_smem(apply_kernel<T, DIM, NP, false>, smem)) return PMG_ECUDA;
+    count_launch(); apply_kernel<T, DIM, NP, false><<<(unsigned)blocks, S::THREADS, smem, s>>>(dm, at, u, f, v);
+  }
+  return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
+}
+
+template <typename T>
+int launch_apply(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f, T* v,
+                 cudaStream_t s) {
+  if (dm.nelem == 0) return PMG_OK;
+#define PMG_APPLY_CASE(DIMV, NPV) \
+  if (dm.dim == DIMV && dm.NP == NPV) return apply_dispatch<T, DIMV, NPV>(dm, at, u, f, v, s);
+  PMG_APPLY_CASE(3, 2) PMG_APPLY_CASE(3, 3) PMG_APPLY_CASE(3, 5) PMG_APPLY_CASE(3, 9)
+  PMG_APPLY_CASE(3, 17)
+  PMG_APPLY_CASE(2, 2) PMG_APPLY_CASE(2, 3) PMG_APPLY_CASE(2, 5) PMG_APPLY_CASE(2, 9)
+  PMG_APPLY_CASE(2, 17) PMG_APPLY_CASE(2, 33)
+#undef PMG_APPLY_CASE
+  return PMG_EINVAL;
+}
+template int launch_apply<double>(const LevelDims&, const ApplyTables<double>&, const double*,
+                                  const double*, double*, cudaStream_t);
+template int launch_apply<float>(const LevelDims&, const ApplyTables<float>&, const float*,
+                                 const float*, float*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// g = M f: diagonal GLL mass (Sec. 2.4 right-hand side)
+// ---------------------------------------------------------------------------
+__global__ void mass_kernel(LevelDims dm, ApplyTables<double> at, const double* __restrict__ f,
+                            double* __restrict__ g) {
+  const int NP = dm.NP;
+  const long long nodes = (dm.dim == 3) ? (long long)NP * NP * NP : (long long)NP * NP;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < dm.ndof;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long e = t / nodes;
+    int n = (int)(t % nodes);
+    int i = n % NP, j = (n / NP) % NP, k = n / (NP * NP);
+    int mx = (int)(e % dm.ne[0]), my = (int)((e / dm.ne[0]) % dm.ne[1]);
+    int mz = (int)(e / ((long long)dm.ne[0] * dm.ne[1]));
+    double s = at.M[0][(size_t)mx * NP + i] * at.M[1][(size_t)my * NP + j];
+    if (dm.dim == 3) s *= at.M[2][(size_t)mz * NP + k];
+    g[t] = s * f[t];
+  }
+}
+
+void launch_mass(const LevelDims& dm, const ApplyTables<double>& at, const double* f, double* g,
+                 cudaStream_t s) {
+  long long blocks = (dm.ndof + 255) / 256;
+  if (blocks > 65535 * 8) blocks = 65535 * 8;
+  count_launch(); mass_kernel<<<(unsigned)blocks, 256, 0, s>>>(dm, at, f, g);
+}
+
+// ---------------------------------------------------------------------------
+// Transfers (Sec. 3.2): prolongation u_f += (J (x) J (x) J) u_c, restriction
+// f_c = (J (x) J (x) J)^T r_f, element by element.  J is NPF x NPC, row-major.
+// One CTA per element; three passes through shared memory.
+// ---------------------------------------------------------------------------
+template <typename T, int DIM, int NPF, int NPC, bool PROLONG>
+__global__ void __launch_bounds__(256)
+transfer_kernel(long long nelem, const T* __restrict__ J, const T* __restrict__ in,
+                T* __restrict__ out) {
+  constexpr int NIN = PROLONG ? NPC : NPF;      // per-axis size of the input
+  constexpr int NOUT = PROLONG ? NPF : NPC;
+  constexpr int NZI = (DIM == 3) ? NIN : 1;
+  constexpr int NZO = (DIM == 3) ? NOUT : 1;
+  extern __shared__ __align__(16) unsigned char tr_smem[];
+  T* sJ = reinterpret_cast<T*>(tr_smem);
+  T* b0 = sJ + NPF * NPC;
+  T* b1 = b0 + NIN * NIN * NZI;
+  T* b2 = b1 + NOUT * NIN * NZI;
+  const long long e = blockIdx.x;
+  for (int t = threadIdx.x; t < NPF * NPC; t += blockDim.x) sJ[t] = J[t];
+  for (int t = threadIdx.x; t < NIN * NIN * NZI; t += blockDim.x)
+    b0[t] = in[e * (NIN * NIN * NZI) + t];
+  __syncthreads();
+  // matrix entry mapping input index a -> output index o along one axis
+  auto Jm = [&](int o, int a) { return PROLONG ? sJ[o * NPC + a] : sJ[a * NPC + o]; };
+  for (int t = threadIdx.x; t < NOUT * NIN * NZI; t += blockDim.x) {   // x pass
+    int o = t % NOUT, rest = t / NOUT;
+    T s = 0;
+#pragma unroll
+    for (int a = 0; a < NIN; ++a) s = fma(Jm(o, a), b0[rest * NIN + a], s);
+    b1[t] = s;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NOUT * NOUT * NZI; t += blockDim.x) {  // y pass
+    int i = t % NOUT, o = (t / NOUT) % NOUT, c = t / (NOUT * NOUT);
+    T s = 0;
+#pragma unroll
+    for (int a = 0; a < NIN; ++a) s = fma(Jm(o, a), b1[(c * NIN + a) * NOUT + i], s);
+    b2[t] = s;
+  }
+  __syncthreads();
+  if (DIM == 2) {
+    for (int t = threadIdx.x; t < NOUT * NOUT; t += blockDim.x) {
+      long long g = e * (NOUT * NOUT) + t;
+      if (PROLONG) out[g] += b2[t];
+      else out[g] = b2[t];
+    }
+    return;
+  }
+  for (int t = threadIdx.x; t < NOUT * NOUT * NZO; t += blockDim.x) {  // z pass
+    int ij = t % (NOUT * NOUT), o = t / (NOUT * NOUT);
+    T s = 0;
+#pragma unroll
+    for (int a = 0; a < NIN; ++a) s = fma(Jm(o, a), b2[a * NOUT * NOUT + ij], s);
+    long long g = e * (NOUT * NOUT * NZO) + t;
+    if (PROLONG) out[g] += s;
+    else out[g] = s;
+  }
+}
+
+template <typename T, bool PROLONG>
+static int transfer_launch(const LevelDims& fine, const LevelDims& coarse, const T* J, const T* in,
+                           T* out, cudaStream_t s) {
+  if (fine.nelem == 0) return PMG_OK;
+  unsigned blocks = (unsigned)fine.nelem;
+#define PMG_TR_CASE(DIMV, NPF, NPC) \
+  if (fine.dim == DIMV && fine.NP == NPF && coarse.NP == NPC) { \
+    constexpr int NIN = PROLONG ? NPC : NPF, NOUT = PROLONG ? NPF : NPC; \
+    constexpr int NZI = DIMV == 3 ? NIN : 1; \
+    const size_t smem = sizeof(T) * (NPF * NPC + NIN * NIN * NZI + NOUT * NIN * NZI + NOUT * NOUT * NZI); \
+    if (!set_smem(transfer_kernel<T, DIMV, NPF, NPC, PROLONG>, smem)) return PMG_ECUDA; \
+    count_launch(); transfer_kernel<T, DIMV, NPF, NPC, PROLONG><<<blocks, 256, smem, s>>>(fine.nelem, J, in, out); \
+    return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA; }
+  PMG_TR_CASE(3, 3, 2) PMG_TR_CASE(3, 5, 3) PMG_TR_CASE(3, 9, 5) PMG_TR_CASE(3, 17, 9)
+  PMG_TR_CASE(2, 3, 2) PMG_TR_CASE(2, 5, 3) PMG_TR_CASE(2, 9, 5) PMG_TR_CASE(2, 17, 9)
+  PMG_TR_CASE(2, 33, 17)
+#undef PMG_TR_CASE
+  return PMG_EINVAL;
+}
+
+template <typename T>
+int launch_restrict(const LevelDims& fine, const LevelDims& coarse, const T* J, const T* rf, T* fc,
+                    cudaStream_t s) {
+  return transfer_launch<T, false>(fine, coarse, J, rf, fc, s);
+}
+template <typename T>
+int launch_prolong(const LevelDims& fine, const LevelDims& coarse, const T* J, const T* uc, T* uf,
+                   cudaStream_t s) {
+  return transfer_launch<T, true>(fine, coarse, J, uc, uf, s);
+}
+template int launch_restrict<double>(const LevelDims&, const LevelDims&, const double*,
+                                     const double*, double*, cudaStream_t);
+template int launch_restrict<float>(const LevelDims&, const LevelDims&, const float*, const float*,
+                                    float*, cudaStream_t);
+template int launch_prolong<double>(const LevelDims&, const LevelDims&, const double*,
+                                    const double*, double*, cudaStream_t);
+template int launch_prolong<float>(const LevelDims&, const LevelDims&, const float*, const float*,
+                                   float*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Exact coarse solve at P = 1 (A_0^+ f_0): the coarse operator is
+// M3(x)M2(x)L1 + M3(x)L2(x)M1 + L3(x)M2(x)M1 with global 1-D factors, so
+// A_0^{-1} = (S3(x)S2(x)S1) (sum Lambda)^{-1} (S3(x)S2(x)S1)^T  -- the fast
+// diagonalisation of Sec. 3.1 applied to the whole coarse grid.  The zero mode
+// of a periodic grid (all three lambda = 0) is dropped (pseudo-inverse).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long coarse_off(const LevelDims& dm, int X, int Y, int Z) {
+  int ex = X >> 1, i = X & 1, ey = Y >> 1, j = Y & 1;
+  if (dm.dim == 2) return ((long long)ey * dm.ne[0] + ex) * 4 + j * 2 + i;
+  int ez = Z >> 1, k = Z & 1;
+  return (((long long)ez * dm.ne[1] + ey) * dm.ne[0] + ex) * 8 + (k * 2 + j) * 2 + i;
+}
+
+__global__ void coarse_axis_kernel(LevelDims dm, int axis, int transpose, const double* __restrict__ S,
+                                   int N, const double* __restrict__ in, double* __restrict__ out) {
+  const int NX = dm.ne[0] * 2, NY = dm.ne[1] * 2, NZ = (dm.dim == 3) ? dm.ne[2] * 2 : 1;
+  const long long total = (long long)NX * NY * NZ;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int X = (int)(t % NX), Y = (int)((t / NX) % NY), Z = (int)(t / ((long long)NX * NY));
+    int o = axis == 0 ? X : (axis == 1 ? Y : Z);
+    double s = 0.0;
+    for (int a = 0; a < N; ++a) {
+      int XX = axis == 0 ? a : X, YY = axis == 1 ? a : Y, ZZ = axis == 2 ? a : Z;
+      double m = transpose ? S[(size_t)a * N + o] : S[(size_t)o * N + a];
+      s = fma(m, in[coarse_off(dm, XX, YY, ZZ)], s);
+    }
+    out[coarse_off(dm, X, Y, Z)] = s;
+  }
+}
+
+__global__ void coarse_scale_kernel(LevelDims dm, const double* __restrict__ lx,
+                                    const double* __restrict__ ly, const double* __restrict__ lz,
+                                    double tol, double* __restrict__ x) {
+  const int NX = dm.ne[0] * 2, NY = dm.ne[1] * 2, NZ = (dm.dim == 3) ? dm.ne[2] * 2 : 1;
+  const long long total = (long long)NX * NY * NZ;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int X = (int)(t % NX), Y = (int)((t / NX) % NY), Z = (int)(t / ((long long)NX * NY));
+    double l = lx[X] + ly[Y] + (dm.dim == 3 ? lz[Z] : 0.0);
+    long long o = coarse_off(dm, X, Y, Z);
+    x[o] = (l > tol) ? x[o] / l : 0.0;
+  }
+}
+
+int launch_coarse_fdm(const LevelDims& dm, const CoarseFdm& c, const double* f, double* u,
+                      cudaStream_t s) {
+  long long total = dm.ndof;
+  unsigned blocks = (unsigned)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  const double* src = f;
+  double* bufs[2] = {c.tmp[0], c.tmp[1]};
+  int cur = 0;
+  for (int d = 0; d < dm.dim; ++d) {          // forward: S_d^T along each axis
+    count_launch(); coarse_axis_kernel<<<blocks, 256, 0, s>>>(dm, d, 1, c.S[d], c.N[d], src, bufs[cur]);
+    src = bufs[cur];
+    cur ^= 1;
+  }
+  count_launch(); coarse_scale_kernel<<<blocks, 256, 0, s>>>(dm, c.lam[0], c.lam[1], dm.dim == 3 ? c.lam[2] : c.lam[0],
+                                             1e-13 * c.lam_max, bufs[cur ^ 1]);
+  for (int d = dm.dim - 1; d >= 0; --d) {     // backward: S_d
+    double* dst = (d == 0) ? u : bufs[cur];
+    count_launch(); coarse_axis_kernel<<<blocks, 256, 0, s>>>(dm, d, 0, c.S[d], c.N[d], src, dst);
+    src = dst;
+    cur ^= 1;
+  }
+  return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Vector kernels of Algorithm 2.  Reductions are deterministic: fixed grid,
+// per-block partial sums in a fixed order, final sum by the last block to
+// finish (threadfence + counter), also in a fixed order.
+// ---------------------------------------------------------------------------
+template <typename Ta, typename Tb>
+__global__ void convert_kernel(const Ta* __restrict__ in, Tb* __restrict__ out, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    out[t] = (Tb)in[t];
+}
+template <typename Ta, typename Tb>
+void launch_convert(const Ta* in, Tb* out, long long n, cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks < 1) blocks = 1;
+  count_launch(); convert_kernel<Ta, Tb><<<(unsigned)blocks, 256, 0, s>>>(in, out, n);
+}
+template void launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-level sum of two values in fixed order; result valid in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double sa[32], sb[32];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sa[w] = a; sb[w] = b; }
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+    a = l < nw ? sa[l] : 0.0;
+    b = l < nw ? sb[l] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+  }
+}
+
+// Final reduction of the per-block partials by the last block; out[0..1].
+__device__ void finish_reduce(double a, double b, double* partial, unsigned* counter, double* out,
+                              int* status, int check) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = a;
+    partial[2 * blockIdx.x + 1] = b;
+    __threadfence();
+    unsigned prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double sa = 0.0, sb = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    sa += ((volatile double*)partial)[2 * i];
+    sb += ((volatile double*)partial)[2 * i + 1];
+  }
+  block_sum2(sa, sb);
+  if (threadIdx.x == 0) {
+    out[0] = sa;
+    out[1] = sb;
+    if (check && status && !(sa == sa && sa < 1e300)) *status = PMG_ENAN;
+    *counter = 0u;
+  }
+}
+
+// out[0] = x.y ; out[1] = x.y2 (y2 may be null -> 0)
+__global__ void dot_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                           const double* __restrict__ y2, long long n, double* partial,
+                           unsigned* counter, double* out) {
+  double a = 0.0, b = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    double xv = x[t];
+    a = fma(xv, y[t], a);
+    if (y2) b = fma(xv, y2[t], b);
+  }
+  block_sum2(a, b);
+  finish_reduce(a, b, partial, counter, out, nullptr, 0);
+}
+
+void launch_dot(const double* x, const double* y, const double* y2, long long n, double* partial,
+                unsigned* counter, double* out, int nblocks, cudaStream_t s) {
+  count_launch(); dot_kernel<<<nblocks, 256, 0, s>>>(x, y, y2, n, partial, counter, out);
+}
+
+// alpha = delta / (p.q); u += alpha p; [r_old = r]; r -= alpha q; out_rr[0] = r.r
+__global__ void cg_update_kernel(double* __restrict__ u, double* __restrict__ r,
+                                 double* __restrict__ r_old, const double* __restrict__ p,
+                                 const double* __restrict__ q, const double* __restrict__ scal,
+                                 int save_old, long long n, double* partial, unsigned* counter,
+                                 double* out_rr, int* status) {
+  const double pq = scal[S_PQ];
+  const double alpha = scal[S_DELTA] / pq;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && status) {
+    if (!(pq > 0.0) || !(scal[S_DELTA] > 0.0)) *status = (pq == pq) ? PMG_EBREAKDOWN : PMG_ENAN;
+  }
+  double a = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    u[t] = fma(alpha, p[t], u[t]);
+    double rv = r[t];
+    if (save_old) r_old[t] = rv;
+    rv = fma(-alpha, q[t], rv);
+    r[t] = rv;
+    a = fma(rv, rv, a);
+  }
+  double b = 0.0;
+  block_sum2(a, b);
+  finish_reduce(a, b, partial, counter, out_rr, status, 1);
+}
+
+void launch_cg_update(double* u, double* r, double* r_old, const double* p, const double* q,
+                      const double* scal, int save_old, long long n, double* partial,
+                      unsigned* counter, double* out_rr, int* status, int nblocks, cudaStream_t s) {
+  count_launch(); cg_update_kernel<<<nblocks, 256, 0, s>>>(u, r, r_old, p, q, scal, save_old, n, partial, counter,
+                                           out_rr, status);
+}
+
+// beta = (z.r - z.r_old) / delta_old ; p = z + beta p   (reading C8; first: r_old = 0)
+__global__ void p_update_kernel(double* __restrict__ p, const double* __restrict__ z,
+                                const double* __restrict__ scal, int first, long long n) {
+  const double zro = first ? 0.0 : scal[S_ZRO];
+  const double beta = (scal[S_ZR] - zro) / scal[S_DELTA];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    p[t] = fma(beta, p[t], z[t]);
+}
+
+void launch_p_update(double* p, const double* z, const double* scal, int first, long long n,
+                     cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  count_launch(); p_update_kernel<<<(unsigned)blocks, 256, 0, s>>>(p, z, scal, first, n);
+}
+
+// delta <- z.r (after the p update, which still needed the old delta)
+__global__ void set_delta_kernel(double* scal, int* status) {
+  scal[S_DELTA] = scal[S_ZR];
+  if (status && !(scal[S_ZR] > 0.0)) *status = (scal[S_ZR] == scal[S_ZR]) ? PMG_EBREAKDOWN : PMG_ENAN;
+}
+void launch_set_delta(double* scal, int* status, cudaStream_t s) {
+  count_launch(); set_delta_kernel<<<1, 1, 0, s>>>(scal, status);
+}
+
+// x -= mean(x)   (projection onto range(A) for periodic grids)
+__global__ void sum_kernel(const double* __restrict__ x, long long n, double* partial,
+                           unsigned* counter, double* out) {
+  double a = 0.0, b = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    a += x[t];
+  block_sum2(a, b);
+  finish_reduce(a, b, partial, counter, out, nullptr, 0);
+}
+__global__ void sub_kernel(double* __restrict__ x, long long n, const double* __restrict__ sum) {
+  const double m = sum[0] / (double)n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    x[t] -= m;
+}
+void launch_sub_mean(double* x, long long n, double* partial, unsigned* counter, double* scal,
+                     int nblocks, cudaStream_t s) {
+  count_launch(); sum_kernel<<<nblocks, 256, 0, s>>>(x, n, partial, counter, scal + S_MEAN);
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  count_launch(); sub_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, n, scal + S_MEAN);
+}
+
+}  // namespace pmg

@@ -1,0 +1,197 @@
+// Internal data structures of the GB300 p-multigrid DG Poisson library.
+//
+// Method: Stiller, "Robust multigrid for high-order discontinuous Galerkin
+// methods" (arXiv 1603.02524).  Host-side set-up (setup.cpp) builds, per
+// p-level and axis, the 1-D operator blocks of Eq. (L:generic), the patch
+// eigen-tables of the fast diagonalisation (Sec. 3.1) and the embedded
+// interpolation (Sec. 3.2); the CUDA kernels (kernels_*.cu) run every
+// per-iteration step; solver.cu orchestrates Algorithms 1 and 2.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pmg.h"
+
+namespace pmg {
+
+// process-wide count of kernel launches (pmg_kernel_launches)
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+constexpr int kMaxLevels = 7;     // P <= 32 -> levels P_l = 1, 2, 4, ..., 32
+
+// ---------------------------------------------------------------------------
+// host-side 1-D discretisation of one axis at one order (Sec. 2.4)
+// ---------------------------------------------------------------------------
+struct Axis1DHost {
+  int P = 0, NP = 0, Ne = 0;
+  bool periodic = false;
+  double beta = 0.0, mu_star = 1.0;
+  std::vector<double> dx;        // element widths
+  std::vector<double> eta, rho;  // GLL nodes / weights
+  std::vector<double> D;         // D[i*NP+k] = phi_k'(eta_i)
+  std::vector<double> Ls;        // standard stiffness
+  // per element m: blocks of Eq. (L:generic) (walls folded into L0, reading C2)
+  std::vector<double> L0, Lm, Lp;   // [Ne][NP][NP]
+  std::vector<double> M;            // [Ne*NP] diagonal mass
+  // rank form of the neighbour coupling used by the apply kernel:
+  // (L^- u^-)_i = -aL D_{0,i} u^-_P + d_{i0} (bL (D u^-)_P - cL u^-_P)
+  // (L^+ u^+)_i =  aR D_{P,i} u^+_0 - d_{iP} (bR (D u^+)_0 + cR u^+_0)
+  std::vector<double> cpl;          // [Ne][8] = aL bL cL hasL aR bR cR hasR
+  double entry(int I, int J) const; // global 1-D stiffness entry L(I, J)
+};
+
+// ---------------------------------------------------------------------------
+// device tables of one level
+// ---------------------------------------------------------------------------
+template <typename T>
+struct ApplyTables {
+  const T* L0[3];     // [Ne_d][NP][NP]
+  const T* M[3];      // [Ne_d][NP]
+  const T* cpl[3];    // [Ne_d][8]
+  const T* D0;        // D_{0,k}
+  const T* DP;        // D_{P,k}
+};
+
+// One axis of a family of patches (EA, or FA with this axis normal/lateral).
+template <typename T>
+struct FdmAxis {
+  int n;          // patch length along this axis
+  int count;      // number of patch positions
+  int start0;     // first global 1-D index of patch p: start0 + p * NP
+  int N;          // global 1-D size Ne * NP (1 for the trivial z axis in 2-D)
+  int periodic;
+  int phys;       // physical axis (0 x, 1 y, 2 z) this patch-buffer axis maps to
+  const T* S;     // [count][n][n]  S[p][a][i]: node a, mode i
+  const T* lam;   // [count][n]
+  const T* w;     // [count][n]
+};
+
+template <typename T>
+struct FdmFamily {
+  FdmAxis<T> ax[3];    // patch-buffer axes a (fastest), b, c
+  int count_total;
+};
+
+struct LevelDims {
+  int dim, P, NP, NPz;       // NPz = NP (3-D) or 1 (2-D)
+  int ne[3];                 // elements per axis (ne[2] = 1 in 2-D)
+  long long nelem, ndof;
+  int periodic;
+};
+
+// all device allocations of one level, for one scalar type
+template <typename T>
+struct LevelDev {
+  ApplyTables<T> at{};
+  FdmFamily<T> ea{};
+  FdmFamily<T> fa[3]{};
+  T* u = nullptr;      // level solution / correction
+  T* f = nullptr;      // level right-hand side
+  T* r = nullptr;      // residual scratch
+  std::vector<void*> owned;
+};
+
+struct CoarseFdm {            // exact global fast-diagonalisation solve at P = 1
+  int N[3];                   // global 1-D sizes (2 Ne_d)
+  double* S[3];               // [N][N] (node, mode)
+  double* lam[3];             // [N]
+  double* tmp[2];
+  double lam_max;
+};
+
+struct Grid {
+  int dim = 3, P = 1, bc_periodic = 0;
+  int ne[3] = {1, 1, 1};
+  std::vector<double> spacing[3];
+  double mu_star = 1.0;
+  double beta[3] = {0, 0, 0};
+};
+
+struct Hier {
+  Grid grid;
+  pmg_options opt{};
+  int L = 0;                       // finest level index
+  LevelDims dims[kMaxLevels];
+  std::vector<Axis1DHost> axes[kMaxLevels];   // per level, per axis
+  int No[kMaxLevels];
+  LevelDev<double> d64[kMaxLevels];
+  LevelDev<float> d32[kMaxLevels];
+  bool has32 = false;
+  // interpolation J_l (fine NP x coarse NP), l = 1..L
+  double* J64[kMaxLevels] = {};
+  float* J32[kMaxLevels] = {};
+  CoarseFdm coarse{};
+  // MGCG work vectors (fine level, fp64)
+  double *r = nullptr, *r_old = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;
+  double* scal = nullptr;          // device scalars
+  double* partial = nullptr;       // reduction partials
+  unsigned* counter = nullptr;     // last-block counter
+  int* dstatus = nullptr;          // device status word
+  double* hscal = nullptr;         // pinned host mirror of the scalars
+  double *g_host_stage = nullptr, *u_host_stage = nullptr;   // device buffers for solve_host
+  std::vector<void*> owned;
+  std::string err;
+  int nsm = 152;
+};
+
+// scalar slots
+// (reductions write two consecutive slots)
+enum { S_DELTA = 0, S_PQ = 2, S_RR = 4, S_ZR = 6, S_ZRO = 7, S_MEAN = 8, S_RR0 = 10, S_NUM = 16 };
+
+// ----------------------------------------------------------------------------
+// set-up (setup.cpp)
+// ----------------------------------------------------------------------------
+void build_axis(Axis1DHost& a, int P, const std::vector<double>& dx, bool periodic, double beta,
+                double mu_star);
+void gll_nodes(int P, std::vector<double>& eta, std::vector<double>& rho);
+void lagrange_matrix(const std::vector<double>& nodes, const std::vector<double>& x,
+                     std::vector<double>& B);
+int sym_eig_jacobi(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& lam);
+int overlap_nodes(int P_l, int policy);
+double transition(double x, int weighting);
+// patch tables along one axis: n, count, start0, and S/lam/w host arrays
+void ec_axis_tables(const Axis1DHost& a, int No, int weighting, int& n, int& count, int& start0,
+                    std::vector<double>& S, std::vector<double>& lam, std::vector<double>& w);
+void fc_axis_tables(const Axis1DHost& a, int weighting, int& n, int& count, int& start0,
+                    std::vector<double>& S, std::vector<double>& lam, std::vector<double>& w);
+void global_axis_eig(const Axis1DHost& a, std::vector<double>& S, std::vector<double>& lam);
+
+// ----------------------------------------------------------------------------
+// kernels (launch wrappers)
+// ----------------------------------------------------------------------------
+template <typename T>
+int launch_apply(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f, T* v,
+                 cudaStream_t s);
+template <typename T>
+int launch_fdm(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, T omega,
+               cudaStream_t s);
+template <typename T>
+int launch_restrict(const LevelDims& fine, const LevelDims& coarse, const T* J, const T* rf, T* fc,
+                    cudaStream_t s);
+template <typename T>
+int launch_prolong(const LevelDims& fine, const LevelDims& coarse, const T* J, const T* uc, T* uf,
+                   cudaStream_t s);
+int launch_coarse_fdm(const LevelDims& dm, const CoarseFdm& c, const double* f, double* u,
+                      cudaStream_t s);
+template <typename Ta, typename Tb>
+void launch_convert(const Ta* in, Tb* out, long long n, cudaStream_t s);
+void launch_dot(const double* x, const double* y, const double* y2, long long n, double* partial,
+                unsigned* counter, double* out, int nblocks, cudaStream_t s);
+void launch_cg_update(double* u, double* r, double* r_old, const double* p, const double* q,
+                      const double* scal, int save_old, long long n, double* partial,
+                      unsigned* counter, double* out_rr, int* status, int nblocks, cudaStream_t s);
+void launch_p_update(double* p, const double* z, const double* scal, int first, long long n,
+                     cudaStream_t s);
+void launch_set_delta(double* scal, int* status, cudaStream_t s);
+void launch_sub_mean(double* x, long long n, double* partial, unsigned* counter, double* scal,
+                     int nblocks, cudaStream_t s);
+void launch_mass(const LevelDims& dm, const ApplyTables<double>& at, const double* f, double* g,
+                 cudaStream_t s);
+
+}  // namespace pmg

@@ -1,0 +1,419 @@
+// Host-side set-up: GLL nodes, 1-D operator blocks, patch eigen-tables,
+// interpolation matrices.  Runs once in pmg_hierarchy_build; nothing here is
+// on the per-iteration path.
+//
+// Paper: Stiller, arXiv 1603.02524.  Sec. 2.4 (nodal operators), Eq.
+// (L:generic) (block-tridiagonal global 1-D stiffness), Sec. 3.1 (subdomains,
+// fast diagonalisation, weights), Sec. 3.2 (embedded interpolation).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <stdexcept>
+
+#include "pmg_internal.h"
+
+namespace pmg {
+
+// Legendre polynomial L_P and its derivatives at x (three-term recurrence).
+static void legendre(int P, double x, double& Lp, double& dLp, double& d2Lp) {
+  double l0 = 1.0, l1 = x;
+  if (P == 0) {
+    Lp = 1.0; dLp = 0.0; d2Lp = 0.0;
+    return;
+  }
+  for (int n = 1; n < P; ++n) {
+    double l2 = ((2.0 * n + 1.0) * x * l1 - n * l0) / (n + 1.0);
+    l0 = l1;
+    l1 = l2;
+  }
+  Lp = l1;
+  // derivative from (1 - x^2) L_P' = P (L_{P-1} - x L_P); away from +-1 only
+  double one_m = 1.0 - x * x;
+  dLp = P * (l0 - x * l1) / one_m;
+  // Legendre ODE: (1 - x^2) L'' - 2 x L' + P (P+1) L = 0
+  d2Lp = (2.0 * x * dLp - P * (P + 1.0) * Lp) / one_m;
+}
+
+// GLL nodes: -1, the roots of L_P' (Newton from Chebyshev-Gauss-Lobatto
+// guesses), +1; weights rho_i = 2 / (P (P+1) L_P(eta_i)^2).
+void gll_nodes(int P, std::vector<double>& eta, std::vector<double>& rho) {
+  eta.assign(P + 1, 0.0);
+  rho.assign(P + 1, 0.0);
+  eta[0] = -1.0;
+  eta[P] = 1.0;
+  for (int i = 1; i < P; ++i) {
+    double x = -std::cos(M_PI * i / P);
+    for (int it = 0; it < 100; ++it) {
+      double L, dL, d2L;
+      legendre(P, x, L, dL, d2L);
+      double dx = dL / d2L;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    eta[i] = x;
+  }
+  // exact symmetry of the node set
+  for (int i = 0; i <= P / 2; ++i) {
+    double a = 0.5 * (eta[P - i] - eta[i]);
+    eta[i] = -a;
+    eta[P - i] = a;
+  }
+  if (P % 2 == 0) eta[P / 2] = 0.0;
+  for (int i = 0; i <= P; ++i) {
+    double L, dL, d2L;
+    double x = eta[i];
+    // L_P(+-1) = (+-1)^P; otherwise use the recurrence value
+    if (i == 0 || i == P) {
+      L = (i == 0 && (P % 2)) ? -1.0 : 1.0;
+    } else {
+      legendre(P, x, L, dL, d2L);
+    }
+    rho[i] = 2.0 / (P * (P + 1.0) * L * L);
+  }
+}
+
+// Classical GLL differentiation matrix D_ik = phi_k'(eta_i):
+// L_P(eta_i) / (L_P(eta_k) (eta_i - eta_k)) off the diagonal,
+// -P(P+1)/4 and P(P+1)/4 at the two corners, 0 elsewhere on the diagonal.
+static void gll_diff(int P, const std::vector<double>& eta, std::vector<double>& D) {
+  int NP = P + 1;
+  std::vector<double> L(NP);
+  for (int i = 0; i < NP; ++i) {
+    if (i == 0) {
+      L[i] = (P % 2) ? -1.0 : 1.0;
+    } else if (i == P) {
+      L[i] = 1.0;
+    } else {
+      double dL, d2L;
+      legendre(P, eta[i], L[i], dL, d2L);
+    }
+  }
+  D.assign(NP * NP, 0.0);
+  for (int i = 0; i < NP; ++i)
+    for (int k = 0; k < NP; ++k)
+      if (i != k) D[i * NP + k] = L[i] / (L[k] * (eta[i] - eta[k]));
+  D[0] = -P * (P + 1.0) / 4.0;
+  D[P * NP + P] = P * (P + 1.0) / 4.0;
+}
+
+// Barycentric Lagrange interpolation matrix B[i][k] = phi_k(x_i) (nodes -> x).
+void lagrange_matrix(const std::vector<double>& nodes, const std::vector<double>& x,
+                     std::vector<double>& B) {
+  int n = (int)nodes.size(), m = (int)x.size();
+  std::vector<double> bw(n, 1.0);
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      if (j != k) bw[k] /= (nodes[k] - nodes[j]);
+  B.assign((size_t)m * n, 0.0);
+  for (int i = 0; i < m; ++i) {
+    int hit = -1;
+    for (int k = 0; k < n; ++k)
+      if (x[i] == nodes[k]) hit = k;
+    if (hit >= 0) {
+      B[(size_t)i * n + hit] = 1.0;
+      continue;
+    }
+    double den = 0.0;
+    for (int k = 0; k < n; ++k) den += bw[k] / (x[i] - nodes[k]);
+    for (int k = 0; k < n; ++k) B[(size_t)i * n + k] = bw[k] / (x[i] - nodes[k]) / den;
+  }
+}
+
+// Global 1-D operator blocks of one axis (Eq. L:generic, with the Delta x^m
+// reading of the first L^-/L^+ terms and the Dirichlet ghost fold-in).
+void build_axis(Axis1DHost& a, int P, const std::vector<double>& dx, bool periodic, double beta,
+                double mu_star) {
+  a.P = P;
+  a.NP = P + 1;
+  a.Ne = (int)dx.size();
+  a.periodic = periodic;
+  a.beta = beta;
+  a.mu_star = mu_star;
+  a.dx = dx;
+  gll_nodes(P, a.eta, a.rho);
+  gll_diff(P, a.eta, a.D);
+  const int NP = a.NP, Ne = a.Ne;
+  const auto& D = a.D;
+  const auto& rho = a.rho;
+  a.Ls.assign(NP * NP, 0.0);
+  for (int i = 0; i < NP; ++i)
+    for (int k = 0; k < NP; ++k) {
+      double s = 0.0;
+      for (int j = 0; j < NP; ++j) s += rho[j] * D[j * NP + i] * D[j * NP + k];
+      a.Ls[i * NP + k] = s;
+    }
+  a.L0.assign((size_t)Ne * NP * NP, 0.0);
+  a.Lm.assign((size_t)Ne * NP * NP, 0.0);
+  a.Lp.assign((size_t)Ne * NP * NP, 0.0);
+  a.M.assign((size_t)Ne * NP, 0.0);
+  a.cpl.assign((size_t)Ne * 8, 0.0);
+  auto width = [&](int m) {
+    if (m >= 0 && m < Ne) return dx[m];
+    if (periodic) return dx[((m % Ne) + Ne) % Ne];
+    return m < 0 ? dx[0] : dx[Ne - 1];   // ghost element: mirrored width
+  };
+  auto wall = [&](int left_elem) {       // is the face (left_elem | left_elem+1) a wall?
+    return !periodic && (left_elem < 0 || left_elem >= Ne - 1);
+  };
+  // bracket of Eq. (flux:num:sigma) on the face between elements l and l+1
+  auto bracket = [&](int l) {
+    double b = wall(l) ? 0.0 : beta;
+    double ha = width(l), hb = width(l + 1);
+    double mu0 = 1.0 / (2.0 * ha * rho[P]) + 1.0 / (2.0 * hb * rho[0]);
+    return 2.0 * (b * b + b) / (ha * rho[P]) + 2.0 * (b * b - b) / (hb * rho[0]) +
+           mu0 * (1.0 + mu_star);
+  };
+  for (int m = 0; m < Ne; ++m) {
+    const double h = dx[m], hl = width(m - 1), hr = width(m + 1);
+    const double bl = wall(m - 1) ? 0.0 : beta;
+    const double br = wall(m) ? 0.0 : beta;
+    const double cl = bracket(m - 1), cr = bracket(m);
+    double* L0 = &a.L0[(size_t)m * NP * NP];
+    double* Lm = &a.Lm[(size_t)m * NP * NP];
+    double* Lp = &a.Lp[(size_t)m * NP * NP];
+    for (int i = 0; i < NP; ++i)
+      for (int k = 0; k < NP; ++k) {
+        double v = 2.0 / h * a.Ls[i * NP + k];
+        if (k == 0) v += (1 - 2 * bl) / h * D[0 * NP + i];
+        if (i == 0) v += (1 - 2 * bl) / h * D[0 * NP + k];
+        if (i == 0 && k == 0) v += cl;
+        if (k == P) v -= (1 + 2 * br) / h * D[P * NP + i];
+        if (i == P) v -= (1 + 2 * br) / h * D[P * NP + k];
+        if (i == P && k == P) v += cr;
+        L0[i * NP + k] = v;
+        double vm = 0.0, vp = 0.0;
+        if (k == P) vm -= (1 - 2 * bl) / h * D[0 * NP + i];
+        if (i == 0) vm += (1 + 2 * bl) / hl * D[P * NP + k];
+        if (i == 0 && k == P) vm -= cl;
+        if (k == 0) vp += (1 + 2 * br) / h * D[P * NP + i];
+        if (i == P) vp -= (1 - 2 * br) / hr * D[0 * NP + k];
+        if (i == P && k == 0) vp -= cr;
+        Lm[i * NP + k] = vm;
+        Lp[i * NP + k] = vp;
+      }
+    double* c = &a.cpl[(size_t)m * 8];
+    c[0] = (1 - 2 * bl) / h; c[1] = (1 + 2 * bl) / hl; c[2] = cl; c[3] = 1.0;
+    c[4] = (1 + 2 * br) / h; c[5] = (1 - 2 * br) / hr; c[6] = cr; c[7] = 1.0;
+    // Dirichlet walls (reading C2): the ghost element holds u_ghost,k = -u_{P-k};
+    // fold L^- (resp. L^+) applied to the ghost into L0 and drop the coupling.
+    if (!periodic && m == 0) {
+      for (int i = 0; i < NP; ++i)
+        for (int k = 0; k < NP; ++k) L0[i * NP + k] -= Lm[i * NP + (P - k)];
+      std::fill(Lm, Lm + NP * NP, 0.0);
+      c[0] = c[1] = c[2] = c[3] = 0.0;
+    }
+    if (!periodic && m == Ne - 1) {
+      for (int i = 0; i < NP; ++i)
+        for (int k = 0; k < NP; ++k) L0[i * NP + k] -= Lp[i * NP + (P - k)];
+      std::fill(Lp, Lp + NP * NP, 0.0);
+      c[4] = c[5] = c[6] = c[7] = 0.0;
+    }
+    for (int i = 0; i < NP; ++i) a.M[(size_t)m * NP + i] = 0.5 * h * rho[i];
+  }
+}
+
+double Axis1DHost::entry(int I, int J) const {
+  int ma = I / NP, ia = I % NP, mb = J / NP, jb = J % NP;
+  double v = 0.0;
+  for (int r = -1; r <= 1; ++r) {
+    int mm = ma + r;
+    if (periodic) {
+      mm = ((mm % Ne) + Ne) % Ne;
+    } else if (mm < 0 || mm >= Ne) {
+      continue;
+    }
+    if (mm != mb) continue;
+    const std::vector<double>& B = (r == -1) ? Lm : (r == 0 ? L0 : Lp);
+    v += B[(size_t)ma * NP * NP + ia * NP + jb];
+  }
+  return v;
+}
+
+// Cyclic Jacobi eigen-solver for a symmetric n x n matrix A (row-major,
+// destroyed).  V receives the eigenvectors as columns, lam the eigenvalues
+// (ascending).  Returns the number of sweeps, -1 if not converged.
+int sym_eig_jacobi(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& lam) {
+  V.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  double fro = 0.0;
+  for (double x : A) fro += x * x;
+  fro = std::sqrt(fro);
+  int sweep = 0;
+  double off = 0.0;
+  for (; sweep < 60; ++sweep) {
+    off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+    if (std::sqrt(off) <= 1e-16 * fro || off == 0.0) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = A[(size_t)p * n + q];
+        if (apq == 0.0) continue;
+        double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+        // rotation angle that annihilates a_pq: tan(2 theta) = 2 a_pq / (a_qq - a_pp)
+        double theta = (aqq - app) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {        // columns p, q of A
+          double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+          A[(size_t)k * n + p] = c * akp - s * akq;
+          A[(size_t)k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {        // rows p, q of A
+          double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+          A[(size_t)p * n + k] = c * apk - s * aqk;
+          A[(size_t)q * n + k] = s * apk + c * aqk;
+        }
+        A[(size_t)p * n + q] = 0.0;
+        A[(size_t)q * n + p] = 0.0;
+        for (int k = 0; k < n; ++k) {        // accumulate V = V J
+          double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+          V[(size_t)k * n + p] = c * vkp - s * vkq;
+          V[(size_t)k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  lam.resize(n);
+  for (int i = 0; i < n; ++i) lam[i] = A[(size_t)i * n + i];
+  // sort ascending
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int x, int y) { return lam[x] < lam[y]; });
+  std::vector<double> l2(n), V2((size_t)n * n);
+  for (int j = 0; j < n; ++j) {
+    l2[j] = lam[ord[j]];
+    for (int k = 0; k < n; ++k) V2[(size_t)k * n + j] = V[(size_t)k * n + ord[j]];
+  }
+  lam.swap(l2);
+  V.swap(V2);
+  return (sweep < 60 || std::sqrt(off) <= 1e-13 * fro) ? sweep : -1;
+}
+
+int overlap_nodes(int P_l, int policy) {
+  if (policy == PMG_OVERLAP_ZERO) return 0;
+  if (policy == PMG_OVERLAP_LEVEL_FLOOR) return 1 + P_l / 8;
+  return 1 + (P_l + 4) / 8;
+}
+
+// Smoothed sign function phi (Sec. 3.1); sgn outside (-1, 1).
+double transition(double x, int weighting) {
+  if (weighting == PMG_WEIGHT_UNWEIGHTED) return 1.0;
+  if (x >= 1.0) return 1.0;
+  if (x <= -1.0) return -1.0;
+  if (weighting == PMG_WEIGHT_ARITHMETIC) return 0.0;
+  if (weighting == PMG_WEIGHT_CUBIC) return 0.5 * x * (3.0 - x * x);
+  double x2 = x * x;
+  return x * (15.0 + x2 * (-10.0 + 3.0 * x2)) / 8.0;
+}
+
+// Generalised eigen-pairs of one patch axis with a decoupled identity for
+// positions outside the domain (Dirichlet truncation): S^T M S = I.
+static void patch_eig(const Axis1DHost& a, const std::vector<int>& gidx, double* S, double* lam) {
+  int n = (int)gidx.size();
+  std::vector<double> B((size_t)n * n, 0.0), Msq(n, 1.0);
+  for (int p = 0; p < n; ++p) Msq[p] = gidx[p] >= 0 ? std::sqrt(a.M[gidx[p]]) : 1.0;
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q) {
+      double v;
+      if (gidx[p] < 0 || gidx[q] < 0) {
+        v = (p == q) ? 1.0 : 0.0;
+      } else {
+        v = a.entry(gidx[p], gidx[q]);
+      }
+      B[(size_t)p * n + q] = v / (Msq[p] * Msq[q]);
+    }
+  // exact symmetry before Jacobi
+  for (int p = 0; p < n; ++p)
+    for (int q = p + 1; q < n; ++q) {
+      double s = 0.5 * (B[(size_t)p * n + q] + B[(size_t)q * n + p]);
+      B[(size_t)p * n + q] = s;
+      B[(size_t)q * n + p] = s;
+    }
+  std::vector<double> V, l;
+  if (sym_eig_jacobi(n, B, V, l) < 0) throw std::runtime_error("Jacobi eigen-solver did not converge");
+  for (int p = 0; p < n; ++p)
+    for (int i = 0; i < n; ++i) S[(size_t)p * n + i] = V[(size_t)p * n + i] / Msq[p];
+  for (int i = 0; i < n; ++i) lam[i] = l[i];
+}
+
+static int wrap_index(const Axis1DHost& a, int I) {
+  int N = a.Ne * a.NP;
+  if (a.periodic) return ((I % N) + N) % N;
+  return (I < 0 || I >= N) ? -1 : I;
+}
+
+// Element-centred patches along one axis (Sec. 3.1): element m plus N_o node
+// layers of each neighbour: global 1-D range [m NP - N_o, m NP + NP + N_o).
+// Weights w_H (Eq. weight function:ec) with readings C6 and C18.
+void ec_axis_tables(const Axis1DHost& a, int No, int weighting, int& n, int& count, int& start0,
+                    std::vector<double>& S, std::vector<double>& lam, std::vector<double>& w) {
+  const int NP = a.NP, Ne = a.Ne, P = a.P;
+  n = NP + 2 * No;
+  count = Ne;
+  start0 = -No;
+  S.assign((size_t)count * n * n, 0.0);
+  lam.assign((size_t)count * n, 0.0);
+  w.assign((size_t)count * n, 0.0);
+  const double dxi = a.eta[No] + 1.0;
+  for (int m = 0; m < Ne; ++m) {
+    std::vector<int> g(n);
+    for (int t = 0; t < n; ++t) g[t] = wrap_index(a, m * NP - No + t);
+    bool has_left = a.periodic || m > 0, has_right = a.periodic || m < Ne - 1;
+    for (int t = 0; t < n; ++t) {
+      if (g[t] < 0) continue;
+      double xi;
+      if (t < No) {
+        xi = a.eta[P - No + 1 + t] - 2.0;
+      } else if (t < No + NP) {
+        xi = a.eta[t - No];
+      } else {
+        xi = a.eta[t - No - NP] + 2.0;
+      }
+      double wt = 1.0;
+      if (No > 0) {
+        double l = has_left ? transition((1.0 + xi) / dxi, weighting) : 1.0;
+        double r = has_right ? transition((1.0 - xi) / dxi, weighting) : 1.0;
+        wt = 0.5 * (l + r);
+      }
+      w[(size_t)m * n + t] = wt;
+    }
+    patch_eig(a, g, &S[(size_t)m * n * n], &lam[(size_t)m * n]);
+  }
+}
+
+// Face-centred patches, normal axis (Sec. 3.1): face f between elements f-1
+// and f, global 1-D range [f NP - P, f NP + P) (far-face layers excluded).
+// Normal weight w_F = 1/2 [1 + phi(1 - |xi_F|)] (reading C5); walls: C13.
+void fc_axis_tables(const Axis1DHost& a, int weighting, int& n, int& count, int& start0,
+                    std::vector<double>& S, std::vector<double>& lam, std::vector<double>& w) {
+  const int NP = a.NP, Ne = a.Ne, P = a.P;
+  n = 2 * P;
+  count = a.periodic ? Ne : Ne + 1;
+  start0 = -P;
+  S.assign((size_t)count * n * n, 0.0);
+  lam.assign((size_t)count * n, 0.0);
+  w.assign((size_t)count * n, 0.0);
+  for (int f = 0; f < count; ++f) {
+    std::vector<int> g(n);
+    for (int t = 0; t < n; ++t) g[t] = wrap_index(a, f * NP - P + t);
+    for (int t = 0; t < n; ++t) {
+      if (g[t] < 0) continue;
+      // t < P: node t+1 of element f-1 (xi_F = eta - 1); else node t-P of element f (xi_F = eta + 1)
+      double xiF = (t < P) ? a.eta[t + 1] - 1.0 : a.eta[t - P] + 1.0;
+      w[(size_t)f * n + t] = 0.5 * (1.0 + transition(1.0 - std::fabs(xiF), weighting));
+    }
+    patch_eig(a, g, &S[(size_t)f * n * n], &lam[(size_t)f * n]);
+  }
+}
+
+// Generalised eigen-pairs of the whole global 1-D operator (coarse solve).
+void global_axis_eig(const Axis1DHost& a, std::vector<double>& S, std::vector<double>& lam) {
+  int N = a.Ne * a.NP;
+  std::vector<int> g(N);
+  for (int i = 0; i < N; ++i) g[i] = i;
+  S.assign((size_t)N * N, 0.0);
+  lam.assign(N, 0.0);
+  patch_eig(a, g, S.data(), lam.data());
+}
+
+}  // namespace pmg

@@ -1,0 +1,687 @@
+// C ABI, hierarchy construction, V-cycle (Algorithm 1) and inexact
+// multigrid-preconditioned CG (Algorithm 2) of Stiller, arXiv 1603.02524.
+//
+// Every per-iteration step is a kernel launched on the caller's stream; the
+// host only sequences launches and, once per CG iteration, reads the residual
+// norm to test convergence.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <new>
+
+#include "pmg_internal.h"
+
+namespace pmg {
+
+std::atomic<unsigned long long> g_launches{0};
+
+int fdm_dispatch_d3(const LevelDims&, const FdmFamily<double>&, const double*, double*, double,
+                    cudaStream_t);
+int fdm_dispatch_d2(const LevelDims&, const FdmFamily<double>&, const double*, double*, double,
+                    cudaStream_t);
+int fdm_dispatch_f3(const LevelDims&, const FdmFamily<float>&, const float*, float*, float,
+                    cudaStream_t);
+int fdm_dispatch_f2(const LevelDims&, const FdmFamily<float>&, const float*, float*, float,
+                    cudaStream_t);
+
+template <>
+int launch_fdm<double>(const LevelDims& dm, const FdmFamily<double>& fam, const double* r,
+                       double* u, double omega, cudaStream_t s) {
+  return dm.dim == 3 ? fdm_dispatch_d3(dm, fam, r, u, omega, s) : fdm_dispatch_d2(dm, fam, r, u, omega, s);
+}
+template <>
+int launch_fdm<float>(const LevelDims& dm, const FdmFamily<float>& fam, const float* r, float* u,
+                      float omega, cudaStream_t s) {
+  return dm.dim == 3 ? fdm_dispatch_f3(dm, fam, r, u, omega, s) : fdm_dispatch_f2(dm, fam, r, u, omega, s);
+}
+
+namespace {
+
+struct CudaError : std::exception {
+  int code;
+  std::string msg;
+  CudaError(int c, std::string m) : code(c), msg(std::move(m)) {}
+};
+
+#define PMG_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      throw CudaError(e_ == cudaErrorMemoryAllocation ? PMG_ENOMEM : PMG_ECUDA,          \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));               \
+  } while (0)
+
+#define PMG_CHECK(expr)                                                                  \
+  do {                                                                                   \
+    int st_ = (expr);                                                                    \
+    if (st_ != PMG_OK) throw CudaError(st_, std::string(#expr) + " failed");             \
+  } while (0)
+
+template <typename T>
+T* dev_alloc(std::vector<void*>& owned, size_t count) {
+  void* p = nullptr;
+  PMG_CUDA(cudaMalloc(&p, count * sizeof(T) + 16));
+  owned.push_back(p);
+  return static_cast<T*>(p);
+}
+
+template <typename T>
+T* dev_upload(std::vector<void*>& owned, const std::vector<double>& host) {
+  std::vector<T> tmp(host.begin(), host.end());
+  T* d = dev_alloc<T>(owned, tmp.size() ? tmp.size() : 1);
+  if (!tmp.empty()) PMG_CUDA(cudaMemcpy(d, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return d;
+}
+
+// trivial third axis of a 2-D patch family
+template <typename T>
+FdmAxis<T> trivial_axis(std::vector<void*>& owned) {
+  FdmAxis<T> ax{};
+  ax.n = 1;
+  ax.count = 1;
+  ax.start0 = 0;
+  ax.N = 1;
+  ax.periodic = 0;
+  ax.phys = 2;
+  ax.S = dev_upload<T>(owned, {1.0});
+  ax.lam = dev_upload<T>(owned, {0.0});
+  ax.w = dev_upload<T>(owned, {1.0});
+  return ax;
+}
+
+struct AxisTables {
+  int n, count, start0;
+  std::vector<double> S, lam, w;
+};
+
+template <typename T>
+FdmAxis<T> upload_axis(std::vector<void*>& owned, const AxisTables& t, const Axis1DHost& a, int phys) {
+  FdmAxis<T> ax{};
+  ax.n = t.n;
+  ax.count = t.count;
+  ax.start0 = t.start0;
+  ax.N = a.Ne * a.NP;
+  ax.periodic = a.periodic ? 1 : 0;
+  ax.phys = phys;
+  ax.S = dev_upload<T>(owned, t.S);
+  ax.lam = dev_upload<T>(owned, t.lam);
+  ax.w = dev_upload<T>(owned, t.w);
+  return ax;
+}
+
+template <typename T>
+void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTables>& ec,
+                     const std::vector<AxisTables>& fc) {
+  const LevelDims& dm = h.dims[l];
+  auto& ax = h.axes[l];
+  auto& own = dev.owned;
+  for (int d = 0; d < 3; ++d) {
+    int dd = d < dm.dim ? d : 0;
+    dev.at.L0[d] = dev_upload<T>(own, ax[dd].L0);
+    dev.at.M[d] = dev_upload<T>(own, ax[dd].M);
+    dev.at.cpl[d] = dev_upload<T>(own, ax[dd].cpl);
+  }
+  std::vector<double> D0(dm.NP), DP(dm.NP);
+  for (int k = 0; k < dm.NP; ++k) {
+    D0[k] = ax[0].D[0 * dm.NP + k];
+    DP[k] = ax[0].D[(size_t)(dm.NP - 1) * dm.NP + k];
+  }
+  dev.at.D0 = dev_upload<T>(own, D0);
+  dev.at.DP = dev_upload<T>(own, DP);
+  dev.u = dev_alloc<T>(own, dm.ndof);
+  dev.f = dev_alloc<T>(own, dm.ndof);
+  dev.r = dev_alloc<T>(own, dm.ndof);
+  if (l == 0) return;
+  if (h.opt.smoother == PMG_SMOOTHER_EA) {
+    FdmFamily<T> fam{};
+    fam.count_total = 1;
+    for (int q = 0; q < 3; ++q) {
+      if (q < dm.dim) {
+        fam.ax[q] = upload_axis<T>(own, ec[q], ax[q], q);
+        fam.count_total *= ec[q].count;
+      } else {
+        fam.ax[q] = trivial_axis<T>(own);
+      }
+    }
+    dev.ea = fam;
+  } else {
+    for (int nrm = 0; nrm < dm.dim; ++nrm) {
+      FdmFamily<T> fam{};
+      fam.ax[0] = upload_axis<T>(own, fc[nrm], ax[nrm], nrm);
+      fam.count_total = fc[nrm].count;
+      int q = 1;
+      for (int d = 0; d < dm.dim; ++d) {
+        if (d == nrm) continue;
+        fam.ax[q] = upload_axis<T>(own, ec[d], ax[d], d);
+        fam.count_total *= ec[d].count;
+        ++q;
+      }
+      for (; q < 3; ++q) fam.ax[q] = trivial_axis<T>(own);
+      dev.fa[nrm] = fam;
+    }
+  }
+}
+
+int reduce_blocks(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// ---------------------------------------------------------------------------
+// smoothing, V-cycle
+// ---------------------------------------------------------------------------
+template <typename T>
+LevelDev<T>& lev(Hier& h, int l);
+template <>
+LevelDev<double>& lev<double>(Hier& h, int l) { return h.d64[l]; }
+template <>
+LevelDev<float>& lev<float>(Hier& h, int l) { return h.d32[l]; }
+
+// nsteps Schwarz iterations on level l: u updated in place; u_zero says that u
+// is known to be 0 on entry (then the first residual is f itself).
+template <typename T>
+void smooth_level(Hier& h, int l, T* u, const T* f, int nsteps, bool u_zero, cudaStream_t s) {
+  LevelDev<T>& d = lev<T>(h, l);
+  const LevelDims& dm = h.dims[l];
+  const T omega = (T)h.opt.omega;
+  for (int st = 0; st < nsteps; ++st) {
+    if (h.opt.smoother == PMG_SMOOTHER_EA) {
+      const T* r = f;
+      if (!(u_zero && st == 0)) {
+        PMG_CHECK(launch_apply<T>(dm, d.at, u, f, d.r, s));
+        r = d.r;
+      }
+      PMG_CHECK(launch_fdm<T>(dm, d.ea, r, u, omega, s));
+    } else {
+      for (int nrm = 0; nrm < dm.dim; ++nrm) {       // reading C12: same order pre and post
+        const T* r = f;
+        if (!(u_zero && st == 0 && nrm == 0)) {
+          PMG_CHECK(launch_apply<T>(dm, d.at, u, f, d.r, s));
+          r = d.r;
+        }
+        PMG_CHECK(launch_fdm<T>(dm, d.fa[nrm], r, u, omega, s));
+      }
+    }
+  }
+}
+
+int ns_level(const Hier& h, int l, bool post) {
+  int base = post ? h.opt.ns_post : h.opt.ns_pre;
+  return h.opt.variable_v ? base << (h.L - l) : base;
+}
+
+// Algorithm 1 with u_L = 0 on entry: uL = MultigridCycle(0, fL).
+template <typename T>
+void vcycle(Hier& h, const T* fL, T* uL, cudaStream_t s) {
+  const int L = h.L;
+  const T* f[kMaxLevels];
+  T* u[kMaxLevels];
+  for (int l = 0; l < L; ++l) {
+    f[l] = lev<T>(h, l).f;
+    u[l] = lev<T>(h, l).u;
+  }
+  f[L] = fL;
+  u[L] = uL;
+  for (int l = L; l >= 1; --l) {
+    LevelDev<T>& d = lev<T>(h, l);
+    PMG_CUDA(cudaMemsetAsync(u[l], 0, sizeof(T) * h.dims[l].ndof, s));
+    smooth_level<T>(h, l, u[l], f[l], ns_level(h, l, false), true, s);
+    PMG_CHECK(launch_apply<T>(h.dims[l], d.at, u[l], f[l], d.r, s));
+    T* J = nullptr;
+    if constexpr (sizeof(T) == 8) J = (T*)h.J64[l]; else J = (T*)h.J32[l];
+    PMG_CHECK(launch_restrict<T>(h.dims[l], h.dims[l - 1], J, d.r, lev<T>(h, l - 1).f, s));
+  }
+  // coarse grid solution in fp64 (Algorithm 1, A_0^+ f_0)
+  if constexpr (sizeof(T) == 8) {
+    PMG_CHECK(launch_coarse_fdm(h.dims[0], h.coarse, h.d64[0].f, h.d64[0].u, s));
+  } else {
+    launch_convert<float, double>(h.d32[0].f, h.d64[0].f, h.dims[0].ndof, s);
+    PMG_CHECK(launch_coarse_fdm(h.dims[0], h.coarse, h.d64[0].f, h.d64[0].u, s));
+    launch_convert<double, float>(h.d64[0].u, h.d32[0].u, h.dims[0].ndof, s);
+  }
+  for (int l = 1; l <= L; ++l) {
+    T* J = nullptr;
+    if constexpr (sizeof(T) == 8) J = (T*)h.J64[l]; else J = (T*)h.J32[l];
+    PMG_CHECK(launch_prolong<T>(h.dims[l], h.dims[l - 1], J, u[l - 1], u[l], s));
+    smooth_level<T>(h, l, u[l], f[l], ns_level(h, l, true), false, s);
+  }
+}
+
+// z = V-cycle(r) in the hierarchy's precision, fp64 in and out.
+void precondition(Hier& h, const double* r, double* z, cudaStream_t s) {
+  if (h.opt.precision == PMG_PREC_MIXED) {
+    const long long n = h.dims[h.L].ndof;
+    launch_convert<double, float>(r, h.d32[h.L].f, n, s);
+    vcycle<float>(h, h.d32[h.L].f, h.d32[h.L].u, s);
+    launch_convert<float, double>(h.d32[h.L].u, z, n, s);
+  } else {
+    vcycle<double>(h, r, z, s);
+  }
+}
+
+void read_scalars(Hier& h, cudaStream_t s, int* status) {
+  PMG_CUDA(cudaMemcpyAsync(h.hscal, h.scal, sizeof(double) * S_NUM, cudaMemcpyDeviceToHost, s));
+  PMG_CUDA(cudaMemcpyAsync(h.hscal + S_NUM, h.dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PMG_CUDA(cudaStreamSynchronize(s));
+  std::memcpy(status, h.hscal + S_NUM, sizeof(int));
+}
+
+int solve_impl(Hier& h, const double* g, double* u, double rtol, pmg_stats* st, cudaStream_t s) {
+  const int L = h.L;
+  const LevelDims& dm = h.dims[L];
+  const long long n = dm.ndof;
+  const int nb = reduce_blocks(n);
+  PMG_CUDA(cudaMemsetAsync(h.dstatus, 0, sizeof(int), s));
+  // r = g - A u (fp64); periodic: project onto range(A)
+  PMG_CHECK(launch_apply<double>(dm, h.d64[L].at, u, g, h.r, s));
+  if (dm.periodic) launch_sub_mean(h.r, n, h.partial, h.counter, h.scal, nb, s);
+  launch_dot(h.r, h.r, nullptr, n, h.partial, h.counter, h.scal + S_RR0, nb, s);
+  int status = 0;
+  read_scalars(h, s, &status);
+  const double r0 = std::sqrt(h.hscal[S_RR0]);
+  if (st) {
+    st->iterations = 0;
+    st->r0 = r0;
+    st->rn = r0;
+    if (st->history) st->history[0] = r0;
+  }
+  if (!(r0 == r0)) return PMG_ENAN;
+  if (r0 == 0.0) return PMG_OK;
+  precondition(h, h.r, h.p, s);
+  launch_dot(h.p, h.r, nullptr, n, h.partial, h.counter, h.scal + S_DELTA, nb, s);
+  int rc = PMG_ENOCONV;
+  for (int it = 1; it <= h.opt.max_iter; ++it) {
+    PMG_CHECK(launch_apply<double>(dm, h.d64[L].at, h.p, nullptr, h.q, s));
+    launch_dot(h.p, h.q, nullptr, n, h.partial, h.counter, h.scal + S_PQ, nb, s);
+    launch_cg_update(u, h.r, h.r_old, h.p, h.q, h.scal, it >= 2 ? 1 : 0, n, h.partial, h.counter,
+                     h.scal + S_RR, h.dstatus, nb, s);
+    read_scalars(h, s, &status);
+    const double rn = std::sqrt(h.hscal[S_RR]);
+    if (st) {
+      st->iterations = it;
+      st->rn = rn;
+      if (st->history) st->history[it] = rn;
+    }
+    if (status != 0) { rc = status; break; }
+    if (rn <= rtol * r0) { rc = PMG_OK; break; }
+    precondition(h, h.r, h.z, s);
+    launch_dot(h.z, h.r, it >= 2 ? h.r_old : nullptr, n, h.partial, h.counter, h.scal + S_ZR, nb, s);
+    launch_p_update(h.p, h.z, h.scal, it == 1 ? 1 : 0, n, s);
+    launch_set_delta(h.scal, h.dstatus, s);
+  }
+  if (dm.periodic) launch_sub_mean(u, n, h.partial, h.counter, h.scal, nb, s);
+  PMG_CUDA(cudaGetLastError());
+  return rc;
+}
+
+Hier* H(pmg_hier h) { return reinterpret_cast<Hier*>(h); }
+Grid* G(pmg_grid g) { return reinterpret_cast<Grid*>(g); }
+
+template <typename F>
+int guarded(Hier* h, F&& fn) {
+  try {
+    return fn();
+  } catch (const CudaError& e) {
+    if (h) h->err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    if (h) h->err = "host allocation failed";
+    return PMG_ENOMEM;
+  } catch (const std::exception& e) {
+    if (h) h->err = e.what();
+    return PMG_EINVAL;
+  }
+}
+
+void free_all(Hier* h) {
+  for (int l = 0; l < kMaxLevels; ++l) {
+    for (void* p : h->d64[l].owned) cudaFree(p);
+    for (void* p : h->d32[l].owned) cudaFree(p);
+  }
+  for (void* p : h->owned) cudaFree(p);
+  if (h->hscal) cudaFreeHost(h->hscal);
+}
+
+}  // namespace
+}  // namespace pmg
+
+using namespace pmg;
+
+extern "C" {
+
+void pmg_options_default(pmg_options* opt) {
+  if (!opt) return;
+  opt->smoother = PMG_SMOOTHER_EA;
+  opt->overlap = PMG_OVERLAP_LEVEL;
+  opt->weighting = PMG_WEIGHT_QUINTIC;
+  opt->ns_pre = 1;
+  opt->ns_post = 1;
+  opt->variable_v = 0;
+  opt->omega = 1.0;
+  opt->precision = PMG_PREC_FP64;
+  opt->max_iter = 100;
+}
+
+int pmg_grid_create(int dim, int P, const int n_elem[3], const double* const spacing[3],
+                    int periodic, double mu_star, const double beta[3], pmg_grid* out) {
+  if (!out || !n_elem || !spacing) return PMG_EINVAL;
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return PMG_EINVAL;
+  if (P < 1 || (P & (P - 1)) != 0 || P > (dim == 3 ? 16 : 32)) return PMG_EINVAL;
+  if (!(mu_star > -1.0)) return PMG_EINVAL;
+  try {
+    Grid* g = new Grid();
+    g->dim = dim;
+    g->P = P;
+    g->bc_periodic = periodic ? 1 : 0;
+    g->mu_star = mu_star;
+    for (int d = 0; d < 3; ++d) {
+      g->ne[d] = d < dim ? n_elem[d] : 1;
+      g->beta[d] = (beta && d < dim) ? beta[d] : 0.0;
+      if (d >= dim) continue;
+      if (g->ne[d] < (periodic ? 2 : 1) || !spacing[d]) { delete g; return PMG_EINVAL; }
+      g->spacing[d].assign(spacing[d], spacing[d] + g->ne[d]);
+      for (double w : g->spacing[d])
+        if (!(w > 0.0) || !std::isfinite(w)) { delete g; return PMG_EINVAL; }
+    }
+    *out = reinterpret_cast<pmg_grid>(g);
+    return PMG_OK;
+  } catch (...) {
+    return PMG_ENOMEM;
+  }
+}
+
+void pmg_grid_destroy(pmg_grid g) { delete G(g); }
+
+int pmg_grid_coords(pmg_grid g, int axis, double* out) {
+  Grid* gr = G(g);
+  if (!gr || !out || axis < 0 || axis >= gr->dim) return PMG_EINVAL;
+  std::vector<double> eta, rho;
+  gll_nodes(gr->P, eta, rho);
+  double left = 0.0;
+  for (int m = 0; m < gr->ne[axis]; ++m) {
+    double w = gr->spacing[axis][m];
+    for (int i = 0; i <= gr->P; ++i) out[m * (gr->P + 1) + i] = left + 0.5 * (eta[i] + 1.0) * w;
+    left += w;
+  }
+  return PMG_OK;
+}
+
+int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
+  if (!g || !out) return PMG_EINVAL;
+  *out = nullptr;
+  Grid* gr = G(g);
+  pmg_options o;
+  if (opt) o = *opt; else pmg_options_default(&o);
+  if (o.smoother != PMG_SMOOTHER_EA && o.smoother != PMG_SMOOTHER_FA) return PMG_EINVAL;
+  if (o.overlap < 0 || o.overlap > 2) return PMG_EINVAL;
+  if (o.weighting != 0 && o.weighting != 1 && o.weighting != 3 && o.weighting != 5) return PMG_EINVAL;
+  if (o.ns_pre < 0 || o.ns_post < 0 || o.max_iter < 1 || !(o.omega > 0.0)) return PMG_EINVAL;
+  if (o.precision != PMG_PREC_FP64 && o.precision != PMG_PREC_MIXED) return PMG_EINVAL;
+  Hier* h = nullptr;
+  try {
+    h = new Hier();
+  } catch (...) {
+    return PMG_ENOMEM;
+  }
+  h->grid = *gr;
+  h->opt = o;
+  int L = 0;
+  while ((1 << L) < gr->P) ++L;
+  h->L = L;
+  int rc = guarded(h, [&]() -> int {
+    int dev = 0;
+    PMG_CUDA(cudaGetDevice(&dev));
+    PMG_CUDA(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int dim = gr->dim;
+    for (int l = 0; l <= L; ++l) {
+      const int Pl = 1 << l;
+      LevelDims& dm = h->dims[l];
+      dm.dim = dim;
+      dm.P = Pl;
+      dm.NP = Pl + 1;
+      dm.NPz = dim == 3 ? Pl + 1 : 1;
+      dm.nelem = 1;
+      for (int d = 0; d < 3; ++d) {
+        dm.ne[d] = gr->ne[d];
+        dm.nelem *= gr->ne[d];
+      }
+      dm.ndof = dm.nelem * dm.NP * dm.NP * dm.NPz;
+      dm.periodic = gr->bc_periodic;
+      h->axes[l].resize(dim);
+      for (int d = 0; d < dim; ++d)
+        build_axis(h->axes[l][d], Pl, gr->spacing[d], gr->bc_periodic != 0, gr->beta[d], gr->mu_star);
+      h->No[l] = overlap_nodes(Pl, o.overlap);
+      std::vector<AxisTables> ec(dim), fc(dim);
+      if (l > 0) {
+        for (int d = 0; d < dim; ++d) {
+          AxisTables& t = ec[d];
+          ec_axis_tables(h->axes[l][d], h->No[l], o.weighting, t.n, t.count, t.start0, t.S, t.lam, t.w);
+          if (o.smoother == PMG_SMOOTHER_FA) {
+            AxisTables& u = fc[d];
+            fc_axis_tables(h->axes[l][d], o.weighting, u.n, u.count, u.start0, u.S, u.lam, u.w);
+          }
+        }
+      }
+      build_level_dev<double>(*h, l, h->d64[l], ec, fc);
+      if (o.precision == PMG_PREC_MIXED) build_level_dev<float>(*h, l, h->d32[l], ec, fc);
+      if (l > 0) {
+        std::vector<double> J;
+        lagrange_matrix(h->axes[l - 1][0].eta, h->axes[l][0].eta, J);
+        h->J64[l] = dev_upload<double>(h->owned, J);
+        h->J32[l] = dev_upload<float>(h->owned, J);
+      }
+    }
+    h->has32 = o.precision == PMG_PREC_MIXED;
+    // exact coarse solve tables (global 1-D eigen-pairs at P = 1)
+    CoarseFdm& c = h->coarse;
+    c.lam_max = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      int dd = d < dim ? d : 0;
+      std::vector<double> S, lam;
+      global_axis_eig(h->axes[0][dd], S, lam);
+      c.N[d] = (int)lam.size();
+      c.S[d] = dev_upload<double>(h->owned, S);
+      c.lam[d] = dev_upload<double>(h->owned, lam);
+      for (double v : lam) c.lam_max = std::max(c.lam_max, std::fabs(v));
+    }
+    c.tmp[0] = dev_alloc<double>(h->owned, h->dims[0].ndof);
+    c.tmp[1] = dev_alloc<double>(h->owned, h->dims[0].ndof);
+    const long long n = h->dims[L].ndof;
+    h->r = dev_alloc<double>(h->owned, n);
+    h->r_old = dev_alloc<double>(h->owned, n);
+    h->p = dev_alloc<double>(h->owned, n);
+    h->q = dev_alloc<double>(h->owned, n);
+    h->z = dev_alloc<double>(h->owned, n);
+    h->scal = dev_alloc<double>(h->owned, S_NUM);
+    h->partial = dev_alloc<double>(h->owned, 2 * 152 * 8 + 64);
+    h->counter = dev_alloc<unsigned>(h->owned, 4);
+    h->dstatus = dev_alloc<int>(h->owned, 4);
+    PMG_CUDA(cudaMemset(h->counter, 0, 4 * sizeof(unsigned)));
+    PMG_CUDA(cudaMemset(h->dstatus, 0, 4 * sizeof(int)));
+    PMG_CUDA(cudaMemset(h->scal, 0, S_NUM * sizeof(double)));
+    PMG_CUDA(cudaMallocHost(&h->hscal, sizeof(double) * (S_NUM + 2)));
+    PMG_CUDA(cudaDeviceSynchronize());
+    return PMG_OK;
+  });
+  if (rc != PMG_OK) {
+    std::fprintf(stderr, "pmg_hierarchy_build: %s\n", h->err.c_str());
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  *out = reinterpret_cast<pmg_hier>(h);
+  return PMG_OK;
+}
+
+void pmg_hierarchy_destroy(pmg_hier hh) {
+  Hier* h = H(hh);
+  if (!h) return;
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+}
+
+int pmg_num_levels(pmg_hier hh) { return hh ? H(hh)->L + 1 : PMG_EINVAL; }
+
+int pmg_level_info(pmg_hier hh, int level, int* P_l, long long* ndof) {
+  Hier* h = H(hh);
+  if (!h || level < 0 || level > h->L) return PMG_EINVAL;
+  if (P_l) *P_l = h->dims[level].P;
+  if (ndof) *ndof = h->dims[level].ndof;
+  return PMG_OK;
+}
+
+int pmg_apply(pmg_hier hh, int level, const double* u, double* Au, void* stream) {
+  Hier* h = H(hh);
+  if (!h || level < 0 || level > h->L || !u || !Au) return PMG_EINVAL;
+  return guarded(h, [&] {
+    return launch_apply<double>(h->dims[level], h->d64[level].at, u, nullptr, Au, (cudaStream_t)stream);
+  });
+}
+
+int pmg_residual(pmg_hier hh, int level, const double* u, const double* f, double* r, void* stream) {
+  Hier* h = H(hh);
+  if (!h || level < 0 || level > h->L || !u || !f || !r) return PMG_EINVAL;
+  return guarded(h, [&] {
+    return launch_apply<double>(h->dims[level], h->d64[level].at, u, f, r, (cudaStream_t)stream);
+  });
+}
+
+int pmg_rhs(pmg_hier hh, const double* f, double* g, void* stream) {
+  Hier* h = H(hh);
+  if (!h || !f || !g) return PMG_EINVAL;
+  return guarded(h, [&] {
+    launch_mass(h->dims[h->L], h->d64[h->L].at, f, g, (cudaStream_t)stream);
+    PMG_CUDA(cudaGetLastError());
+    return PMG_OK;
+  });
+}
+
+int pmg_smooth(pmg_hier hh, int level, double* u, const double* f, int nsteps, void* stream) {
+  Hier* h = H(hh);
+  if (!h || level < 1 || level > h->L || !u || !f || nsteps < 0) return PMG_EINVAL;
+  return guarded(h, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->opt.precision == PMG_PREC_MIXED) {
+      const long long n = h->dims[level].ndof;
+      // level vectors of the V-cycle serve as fp32 staging buffers
+      float* uf = h->d32[level].u;
+      float* ff = h->d32[level].f;
+      launch_convert<double, float>(u, uf, n, s);
+      launch_convert<double, float>(f, ff, n, s);
+      smooth_level<float>(*h, level, uf, ff, nsteps, false, s);
+      launch_convert<float, double>(uf, u, n, s);
+    } else {
+      smooth_level<double>(*h, level, u, f, nsteps, false, s);
+    }
+    PMG_CUDA(cudaGetLastError());
+    return PMG_OK;
+  });
+}
+
+int pmg_restrict(pmg_hier hh, int level, const double* rf, double* fc, void* stream) {
+  Hier* h = H(hh);
+  if (!h || level < 1 || level > h->L || !rf || !fc) return PMG_EINVAL;
+  return guarded(h, [&] {
+    return launch_restrict<double>(h->dims[level], h->dims[level - 1], h->J64[level], rf, fc,
+                                   (cudaStream_t)stream);
+  });
+}
+
+int pmg_prolong(pmg_hier hh, int level, const double* uc, double* uf, void* stream) {
+  Hier* h = H(hh);
+  if (!h || level < 1 || level > h->L || !uc || !uf) return PMG_EINVAL;
+  return guarded(h, [&] {
+    return launch_prolong<double>(h->dims[level], h->dims[level - 1], h->J64[level], uc, uf,
+                                  (cudaStream_t)stream);
+  });
+}
+
+int pmg_coarse_solve(pmg_hier hh, const double* f0, double* u0, void* stream) {
+  Hier* h = H(hh);
+  if (!h || !f0 || !u0) return PMG_EINVAL;
+  return guarded(h, [&] { return launch_coarse_fdm(h->dims[0], h->coarse, f0, u0, (cudaStream_t)stream); });
+}
+
+int pmg_vcycle(pmg_hier hh, const double* f, double* u, void* stream) {
+  Hier* h = H(hh);
+  if (!h || !f || !u) return PMG_EINVAL;
+  return guarded(h, [&] {
+    precondition(*h, f, u, (cudaStream_t)stream);
+    PMG_CUDA(cudaGetLastError());
+    return PMG_OK;
+  });
+}
+
+int pmg_solve(pmg_hier hh, const double* g, double* u, double rtol, pmg_stats* st, void* stream) {
+  Hier* h = H(hh);
+  if (!h || !g || !u || !(rtol >= 0.0)) return PMG_EINVAL;
+  return guarded(h, [&] { return solve_impl(*h, g, u, rtol, st, (cudaStream_t)stream); });
+}
+
+int pmg_solve_host(pmg_hier hh, const double* g_host, double* u_host, double rtol, pmg_stats* st,
+                   void* stream) {
+  Hier* h = H(hh);
+  if (!h || !g_host || !u_host || !(rtol >= 0.0)) return PMG_EINVAL;
+  return guarded(h, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = h->dims[h->L].ndof;
+    if (!h->g_host_stage) {               // first call: device staging buffers
+      h->g_host_stage = dev_alloc<double>(h->owned, n);
+      h->u_host_stage = dev_alloc<double>(h->owned, n);
+    }
+    PMG_CUDA(cudaMemcpyAsync(h->g_host_stage, g_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    PMG_CUDA(cudaMemcpyAsync(h->u_host_stage, u_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    int rc = solve_impl(*h, h->g_host_stage, h->u_host_stage, rtol, st, s);
+    PMG_CUDA(cudaMemcpyAsync(u_host, h->u_host_stage, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PMG_CUDA(cudaStreamSynchronize(s));
+    return rc;
+  });
+}
+
+const char* pmg_status_string(int status) {
+  switch (status) {
+    case PMG_OK: return "ok";
+    case PMG_EINVAL: return "invalid argument or unsupported configuration";
+    case PMG_ENOMEM: return "out of memory";
+    case PMG_ECUDA: return "CUDA error";
+    case PMG_ENOCONV: return "no convergence within max_iter";
+    case PMG_EBREAKDOWN: return "CG breakdown (p^T A p <= 0 or delta <= 0)";
+    case PMG_ENAN: return "non-finite residual";
+    case PMG_ETIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* pmg_last_error(pmg_hier hh) { return hh ? H(hh)->err.c_str() : ""; }
+
+unsigned long long pmg_kernel_launches(void) { return g_launches.load(); }
+
+int pmg_schwarz_sweep(pmg_hier hh, int level, int family, const double* r, double* u, void* stream) {
+  Hier* h = H(hh);
+  if (!h || level < 1 || level > h->L || !r || !u) return PMG_EINVAL;
+  const LevelDims& dm = h->dims[level];
+  const bool ea = h->opt.smoother == PMG_SMOOTHER_EA;
+  if (ea ? family != -1 : (family < 0 || family >= dm.dim)) return PMG_EINVAL;
+  return guarded(h, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->opt.precision == PMG_PREC_MIXED) {
+      LevelDev<float>& d = h->d32[level];
+      launch_convert<double, float>(r, d.r, dm.ndof, s);
+      launch_convert<double, float>(u, d.u, dm.ndof, s);
+      PMG_CHECK(launch_fdm<float>(dm, ea ? d.ea : d.fa[family], d.r, d.u, (float)h->opt.omega, s));
+      launch_convert<float, double>(d.u, u, dm.ndof, s);
+    } else {
+      LevelDev<double>& d = h->d64[level];
+      PMG_CHECK(launch_fdm<double>(dm, ea ? d.ea : d.fa[family], r, u, h->opt.omega, s));
+    }
+    PMG_CUDA(cudaGetLastError());
+    return PMG_OK;
+  });
+}
+
+}  // extern "C"
