@@ -1,0 +1,363 @@
+"""Benchmark: DOF/s of the p-multigrid-preconditioned CG solve to a 1e-10 relative residual.
+
+Workload (default): 3-D Poisson on the unit cube, 16^3 uniform elements, P = 8
+(2 985 984 DOF), interior penalty (mu_star = 1), homogeneous Dirichlet walls,
+f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z) + seeded U[-1, 1] nodal noise, MGCG with
+the element-centred additive Schwarz smoother (level-dependent overlap, quintic
+weights), V(1,1), u_0 = 0, FP64.  One step = one complete solve from u_0 = 0.
+
+The JSON line also reports the Schwarz patch kernel's own throughput and
+roofline fraction, the same solve with the mixed-precision V-cycle, the
+end-to-end number through the host-buffer C-ABI call, the FP64 CPU oracle timed
+on this host on a bounded sample, SM clocks during the timed region and the
+number of library kernels launched there.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own replica (the solve does not
+shard across GPUs); value = all ranks' DOF / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as syn  # noqa: E402
+
+METRIC = "DOF/s to 1e-10 residual (MG-CG solve), smoother GDOF/s and % roofline, vs FP64 plain"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 / FP32 FMA throughput measured on this machine's GB300 (FMA-chain probe, 152 SMs, ~2.0 GHz)
+FP64_PEAK_GFLOPS = 1200.0
+FP32_PEAK_GFLOPS = 74800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2ldg", "c3", "c4"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    if name == "c1":
+        return syn.config1(), dict(smoother="EA", overlap="l")
+    if name == "c2":
+        return syn.config2(0.0), dict(smoother="EA", overlap="l")
+    if name == "c2ldg":
+        return syn.config2(0.5), dict(smoother="EA", overlap="l")
+    if name == "c3":
+        return syn.config3(), dict(smoother="EA", overlap="l")
+    if name == "c4":
+        return syn.config4(), dict(smoother="FA", overlap="l", variable_v=True)
+    raise ValueError(name)
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, dev=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev if dev is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.out = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        med = statistics.median(sm) if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_baseline(w, opts, budget_s=30.0):
+    """The FP64 CPU oracle on a bounded sample of the workload: the same problem on 12^3
+    elements (or the full grid if smaller), complete MGCG solve to 1e-10."""
+    from oracle.layout import to_global
+    from oracle.mg import Hierarchy as OHier, mgcg
+    ne = tuple(min(n, 12) for n in w.n_elem)
+    sp = [syn.uniform_spacing(n, 1.0) if len(set(s)) == 1 else list(s[:n]) for n, s in zip(ne, w.spacing)]
+    sw = syn.Workload(w.name + "_sample", w.dim, w.P, ne, sp, w.periodic, w.beta, w.mu_star, w.rhs, w.seed)
+    t0 = time.perf_counter()
+    h = OHier(w.dim, w.P, sp, w.periodic, w.beta, w.mu_star, smoother=opts["smoother"],
+              overlap=opts["overlap"], variable=opts.get("variable_v", False))
+    d = h.fine
+    F = d.rhs(to_global(syn.source_values(sw, d.coords()), w.dim))
+    t1 = time.perf_counter()
+    U, hist = mgcg(h, np.zeros_like(F), F, rtol=1e-10)
+    t2 = time.perf_counter()
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count()
+    return {"value": d.ndof / (t2 - t1), "unit": "DOF/s", "cores": cores, "kind": "oracle",
+            "sample": f"{'x'.join(map(str, ne))} elements at P={w.P} ({d.ndof} DOF), full MGCG solve to "
+                      f"1e-10 ({len(hist) - 1} iterations, {t2 - t1:.1f} s; set-up {t1 - t0:.1f} s excluded)",
+            "iterations": len(hist) - 1, "seconds": t2 - t1}
+
+
+def run_reference(args):
+    rank, world = dist_init(args)
+    if rank != 0:
+        return
+    w, opts = workload(args.workload)
+    vals = []
+    base = None
+    for k in range(args.warmup + args.steps):
+        r = oracle_baseline(w, opts)
+        if k >= args.warmup:
+            vals.append(r["value"])
+            base = r
+        if args.warmup + args.steps > 2 and k == 0 and r["seconds"] > 40:
+            break
+    if not vals:
+        vals = [r["value"]]
+        base = r
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DOF/s", "n_gpus": 0,
+            "steps": len(vals), "warmup": args.warmup, "ms_per_step": 1e3 * w.ndof / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "sample": base["sample"]},
+            "cpu_baseline": {"value": v, "unit": "DOF/s", "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_1603_02524_gb300 import Grid, Hierarchy, binding
+
+    rank, world = dist_init(args)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = binding.load()
+    w, opts = workload(args.workload)
+    grid = Grid(w.dim, w.P, w.n_elem, w.spacing, periodic=w.periodic, mu_star=w.mu_star, beta=w.beta)
+    h = Hierarchy(grid, precision="fp64", **opts)
+    n = h.ndof()
+    f = syn.source_values(w, [grid.coords(d) for d in range(w.dim)])
+    ft = torch.from_numpy(f.reshape(-1)).to(dev)
+    g = torch.empty_like(ft)
+    h.rhs(ft, g)
+    u = torch.zeros_like(g)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step(hier, uu):
+        uu.zero_()
+        return hier.solve(g, uu, rtol=1e-10, history=False)
+
+    for _ in range(args.warmup):
+        step(h, u)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    launches0 = lib.pmg_kernel_launches()
+    times, iters = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)                     # evict the 24 MB working set from L2 between steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, it, _ = step(h, u)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        iters.append(it)
+        assert rc == 0, f"solve status {rc}"
+    torch.cuda.synchronize()
+    launches = lib.pmg_kernel_launches() - launches0
+    clk = clocks.stop()
+    barrier(world)
+    t_step = max_over_ranks(statistics.mean(times), world, dev)
+    value = world * n / (t_step * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "dim": w.dim, "P": w.P, "n_elem": list(w.n_elem), "ndof": n,
+                       "smoother": opts["smoother"] + "_l", "flux": "IP" if w.beta == 0 else "LDG",
+                       "rtol": 1e-10, "iterations": iters[0], "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas{world}"},
+            "gpu_launches": int(launches), "clocks": clk}
+
+    if not args.no_extras:
+        extras(args, w, opts, grid, h, g, u, dev, stream, line, lib)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def time_kernel(fn, reps, stream, flush):
+    import torch
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
+    import torch
+    from paper_1603_02524_gb300 import Hierarchy, binding
+    n = h.ndof()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    NP = w.P + 1
+    nelem = int(np.prod(w.n_elem))
+    No = 1 + (w.P + 4) // 8
+    nn = NP + 2 * No
+    # --- Schwarz patch kernel alone (EA, finest level): the dominant kernel of the solve
+    r = torch.empty_like(g)
+    h.residual(h.L, torch.zeros_like(g), g, r)
+    uu = torch.zeros_like(g)
+    fam = -1 if opts["smoother"] == "EA" else 0
+
+    def sweep(hier=h, x=uu):
+        st = lib.pmg_schwarz_sweep(hier.handle, hier.L, fam, binding._ptr(r), binding._ptr(x),
+                                   binding._stream(stream))
+        assert st == 0, st
+    sweep()
+    ms = time_kernel(sweep, 10, stream, flush)
+    flops = 12.0 * nn ** 4 * nelem            # 6 line passes of n^4 FMAs per n^3 patch
+    ach = flops / (ms * 1e-3) / 1e12
+    line["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                        "frac": ach / (FP64_PEAK_GFLOPS / 1e3), "traffic": None,
+                        "kernel": f"fdm_kernel<double,{nn},{nn},{nn}> (EA patch solve, P={w.P})",
+                        "peak_source": "FP64 FMA probe on this pool's GB300 (nominal 1.25 TFLOP/s); "
+                                       "FP64 is ALU-bound here: 12 n^4 flop per patch vs 24 B/DOF"}
+    line["smoother"] = {"gdof_s": n / (ms * 1e-3) / 1e9, "ms_patch_sweep": ms,
+                        "note": "EA patch sweep alone (gather, 6 transforms, weighted scatter), FP64"}
+    # apply kernel (FP64): share of the solve
+    ms_apply = time_kernel(lambda: h.apply(h.L, g, r), 10, stream, flush)
+    line["apply"] = {"ms": ms_apply, "gdof_s": n / (ms_apply * 1e-3) / 1e9,
+                     "gflops": (6.0 * NP + 12) * n / (ms_apply * 1e-3) / 1e9}
+    # --- mixed-precision V-cycle (FP32 smoother/transfers/residuals inside FP64 CG)
+    hm = Hierarchy(grid, precision="mixed", **opts)
+    um = torch.zeros_like(g)
+    for _ in range(2):
+        um.zero_()
+        hm.solve(g, um, rtol=1e-10, history=False)
+    tm, itm = [], 0
+    for _ in range(max(2, args.steps)):
+        flush.fill_(1.0)
+        um.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, itm, _ = hm.solve(g, um, rtol=1e-10, history=False)
+        e1.record(stream)
+        e1.synchronize()
+        tm.append(e0.elapsed_time(e1))
+    u.zero_()
+    h.solve(g, u, rtol=1e-10, history=False)
+    rel = float((um - u).abs().max() / u.abs().max())
+    um2 = torch.zeros_like(g)
+
+    def sweep_m():
+        st = lib.pmg_schwarz_sweep(hm.handle, hm.L, fam, binding._ptr(r), binding._ptr(um2),
+                                   binding._stream(stream))
+        assert st == 0
+    ms_m = time_kernel(sweep_m, 10, stream, flush)
+    line["mixed"] = {"value": n / (statistics.mean(tm) * 1e-3), "unit": "DOF/s",
+                     "ms_per_step": statistics.mean(tm), "iterations": itm, "status": rc,
+                     "max_rel_diff_vs_fp64_solution": rel,
+                     "speedup_vs_fp64": statistics.mean(tm) and line["ms_per_step"] / statistics.mean(tm),
+                     "patch_sweep_ms_incl_fp64_fp32_staging": ms_m}
+    hm.close()
+    # --- end to end through the host-buffer C-ABI call (pinned host memory)
+    g_host = g.cpu().pin_memory()
+    u_host = torch.zeros(n, dtype=torch.float64).pin_memory()
+    h.solve_host(g_host, u_host)
+    te = []
+    for _ in range(max(2, args.steps)):
+        u_host.zero_()
+        t0 = time.perf_counter()
+        rc, it = h.solve_host(g_host, u_host, rtol=1e-10)
+        te.append(time.perf_counter() - t0)
+    line["e2e"] = {"value": n / statistics.mean(te), "unit": "DOF/s", "h2d_bytes_per_step": 16 * n,
+                   "d2h_bytes_per_step": 8 * n, "call": "pmg_solve_host (g, u0 in; u out)"}
+    # --- FP64 CPU oracle on this host (bounded sample)
+    if not args.no_cpu and int(os.environ.get("RANK", "0")) == 0:
+        line["cpu_baseline"] = oracle_baseline(w, opts)
+
+
+if __name__ == "__main__":
+    main()

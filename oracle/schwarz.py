@@ -124,7 +124,7 @@ def ec_axis(axis, m, No, weighting):
         dxi = eta[No] + 1.0
         left = phi((1 + xi) / dxi, weighting) if has_left else 1.0       # C18
         right = phi((1 - xi) / dxi, weighting) if has_right else 1.0     # C18
-        w = 0.5 * (left + right)
+        w = 0.5 * (left + right) * np.ones_like(xi)     # both terms may be the wall limit 1
     return AxisPatch(idx, w, axis)
 
 

@@ -25,7 +25,7 @@ EXPORTS = ["pmg_options_default", "pmg_grid_create", "pmg_grid_destroy", "pmg_gr
            "pmg_hierarchy_build", "pmg_hierarchy_destroy", "pmg_num_levels", "pmg_level_info",
            "pmg_apply", "pmg_residual", "pmg_rhs", "pmg_smooth", "pmg_restrict", "pmg_prolong",
            "pmg_coarse_solve", "pmg_vcycle", "pmg_solve", "pmg_solve_host", "pmg_status_string",
-           "pmg_last_error"]
+           "pmg_last_error", "pmg_schwarz_sweep", "pmg_kernel_launches"]
 
 
 class PmgOptions(ctypes.Structure):
@@ -81,6 +81,8 @@ def load(path: str | None = None):
         "pmg_solve_host": (i, [vp, vp, vp, d, ctypes.POINTER(PmgStats), vp]),
         "pmg_status_string": (ctypes.c_char_p, [i]),
         "pmg_last_error": (ctypes.c_char_p, [vp]),
+        "pmg_schwarz_sweep": (i, [vp, i, i, vp, vp, vp]),
+        "pmg_kernel_launches": (ctypes.c_ulonglong, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -219,6 +221,11 @@ class Hierarchy:
         n = self.ndof(0)
         _check("pmg_coarse_solve", load().pmg_coarse_solve(self.handle, _dev(f0, n), _dev(u0, n),
                                                            _stream(stream)), self.handle)
+
+    def schwarz_sweep(self, level, family, r, u, stream=None):
+        n = self.ndof(level)
+        _check("pmg_schwarz_sweep", load().pmg_schwarz_sweep(self.handle, level, family, _dev(r, n), _dev(u, n),
+                                                             _stream(stream)), self.handle)
 
     def vcycle(self, f, u, stream=None):
         n = self.ndof()

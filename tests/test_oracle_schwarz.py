@@ -44,6 +44,15 @@ def test_partition_of_unity(periodic, weighting, P, overlap):
             assert np.abs(_coverage(disc, sm, nrm) - 1).max() < 1e-14
 
 
+def test_partition_of_unity_single_element_axis():
+    # one element between two walls: both transition terms take their wall limit (C18)
+    disc = dg.Discretisation(3, 4, [[0.5, 0.5], [1.0], [0.3, 0.3, 0.4]], False)
+    for kind in ("EA", "FA"):
+        sm = schwarz.Smoother(disc, kind, "l", "quintic")
+        for nrm in ([None] if kind == "EA" else [0, 1, 2]):
+            assert np.abs(_coverage(disc, sm, nrm) - 1).max() < 1e-14
+
+
 def test_patch_sizes():
     disc = dg.Discretisation(2, 8, [[0.25] * 4, [0.25] * 4], True)
     sm = schwarz.Smoother(disc, "FA", "l", "quintic")
