@@ -47,9 +47,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2ldg", "c3", "c4"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2ldg", "c2x32", "c3", "c4"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="arithmetic of the timed solve's V-cycle (the outer CG is always FP64)")
     return ap.parse_args()
 
 
@@ -60,6 +62,10 @@ def workload(name):
         return syn.config2(0.0), dict(smoother="EA", overlap="l")
     if name == "c2ldg":
         return syn.config2(0.5), dict(smoother="EA", overlap="l")
+    if name == "c2x32":      # the 16^3 workload refined to 32^3 elements (vectors > L2): profiling
+        w = syn.config2(0.0)
+        w.name, w.n_elem, w.spacing = "poisson3d_32cube_P8_dirichlet_ip", (32, 32, 32), [syn.uniform_spacing(32, 1.0)] * 3
+        return w, dict(smoother="EA", overlap="l")
     if name == "c3":
         return syn.config3(), dict(smoother="EA", overlap="l")
     if name == "c4":
@@ -204,7 +210,7 @@ def main():
     lib = binding.load()
     w, opts = workload(args.workload)
     grid = Grid(w.dim, w.P, w.n_elem, w.spacing, periodic=w.periodic, mu_star=w.mu_star, beta=w.beta)
-    h = Hierarchy(grid, precision="fp64", **opts)
+    h = Hierarchy(grid, precision=args.precision, **opts)
     n = h.ndof()
     f = syn.source_values(w, [grid.coords(d) for d in range(w.dim)])
     ft = torch.from_numpy(f.reshape(-1)).to(dev)
@@ -244,7 +250,8 @@ def main():
     value = world * n / (t_step * 1e-3)
     line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "data": "synthetic",
             "config": {"workload": w.name, "dim": w.dim, "P": w.P, "n_elem": list(w.n_elem), "ndof": n,
                        "smoother": opts["smoother"] + "_l", "flux": "IP" if w.beta == 0 else "LDG",
                        "rtol": 1e-10, "iterations": iters[0], "l2": "flushed between steps (256 MB write)",
