@@ -158,6 +158,24 @@ int pmg_prolong(pmg_hier h, int level, const double* uc_dev, double* uf_dev, voi
  */
 int pmg_coarse_solve(pmg_hier h, const double* f0_dev, double* u0_dev, void* stream);
 
+/*
+ * pmg_coarse_solve without any device workspace of its own (the paper has no
+ * counterpart; this is a library-integration entry point).  Same arguments,
+ * same result as pmg_coarse_solve; the call allocates nothing.  Its two scratch
+ * vectors live in a fixed 4 MiB device array compiled into the library, so it
+ * suits callers that must not allocate while solving: code recorded into a CUDA
+ * graph by stream capture, or code whose host framework owns all device memory.
+ *  - Limit: the P = 1 problem may have at most 262 144 unknowns (32^3 elements in
+ *    3-D); larger hierarchies get PMG_EINVAL and a message in pmg_last_error.
+ *  - The first call on each device looks up the array's device address; make that
+ *    first call before any stream capture.
+ *  - All calls in the process share the one array per device: calls that may run
+ *    concurrently on the GPU (different streams, different hierarchies) race and
+ *    must be serialised by the caller.
+ * The hierarchy itself (tables, f0/u0 sizes) comes from pmg_hierarchy_build.
+ */
+int pmg_coarse_solve_static(pmg_hier h, const double* f0_dev, double* u0_dev, void* stream);
+
 /* u_dev = MultigridCycle(0, f_dev): one V-cycle of Algorithm 1 on the finest level. */
 int pmg_vcycle(pmg_hier h, const double* f_dev, double* u_dev, void* stream);
 

@@ -25,7 +25,7 @@ EXPORTS = ["pmg_options_default", "pmg_grid_create", "pmg_grid_destroy", "pmg_gr
            "pmg_hierarchy_build", "pmg_hierarchy_destroy", "pmg_num_levels", "pmg_level_info",
            "pmg_apply", "pmg_residual", "pmg_rhs", "pmg_smooth", "pmg_restrict", "pmg_prolong",
            "pmg_coarse_solve", "pmg_vcycle", "pmg_solve", "pmg_solve_host", "pmg_status_string",
-           "pmg_last_error", "pmg_schwarz_sweep", "pmg_kernel_launches"]
+           "pmg_last_error", "pmg_schwarz_sweep", "pmg_kernel_launches", "pmg_coarse_solve_static"]
 
 
 class PmgOptions(ctypes.Structure):
@@ -83,6 +83,7 @@ def load(path: str | None = None):
         "pmg_last_error": (ctypes.c_char_p, [vp]),
         "pmg_schwarz_sweep": (i, [vp, i, i, vp, vp, vp]),
         "pmg_kernel_launches": (ctypes.c_ulonglong, []),
+        "pmg_coarse_solve_static": (i, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
