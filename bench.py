@@ -147,7 +147,9 @@ def oracle_baseline(w, opts, budget_s=30.0):
     elements (or the full grid if smaller), complete MGCG solve to 1e-10."""
     from oracle.layout import to_global
     from oracle.mg import Hierarchy as OHier, mgcg
-    ne = tuple(min(n, 12) for n in w.n_elem)
+    # about 1.2 M unknowns: 12^3 elements at P = 8, 6^3 at P = 16
+    side = max(2, round((1.2e6 / (w.P + 1) ** w.dim) ** (1.0 / w.dim)))
+    ne = tuple(min(n, side) for n in w.n_elem)
     sp = [syn.uniform_spacing(n, 1.0) if len(set(s)) == 1 else list(s[:n]) for n, s in zip(ne, w.spacing)]
     sw = syn.Workload(w.name + "_sample", w.dim, w.P, ne, sp, w.periodic, w.beta, w.mu_star, w.rhs, w.seed)
     t0 = time.perf_counter()
@@ -303,15 +305,22 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
         assert st == 0, st
     sweep()
     ms = time_kernel(sweep, 10, stream, flush)
-    flops = 12.0 * nn ** 4 * nelem            # 6 line passes of n^4 FMAs per n^3 patch
+    # algorithmic flops of one launch as implemented: 2 x the multiply-adds of the six line
+    # passes (even-odd split on centro-symmetric axes), reported by the library
+    flops = 2.0 * h.schwarz_sweep_fma(h.L, fam)
+    paper_flops = 12.0 * nn ** 4 * nelem       # the paper's count: 6 passes of n^4 per n^3 patch
     ach = flops / (ms * 1e-3) / 1e12
     line["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
                         "frac": ach / (FP64_PEAK_GFLOPS / 1e3), "traffic": None,
-                        "kernel": f"fdm_kernel<double,{nn},{nn},{nn}> (EA patch solve, P={w.P})",
-                        "peak_source": "FP64 FMA probe on this pool's GB300 (nominal 1.25 TFLOP/s); "
-                                       "FP64 is ALU-bound here: 12 n^4 flop per patch vs 24 B/DOF"}
+                        "kernel": (f"fdm_kernel<double,{nn},{nn},{nn}> (EA patch solve, P={w.P})"
+                                   if fam == -1 else
+                                   f"fdm_kernel<double,{2 * w.P},{nn},{nn}> (FA patch solve, x faces, P={w.P})"),
+                        "flops_per_launch": flops, "paper_count_flops_per_launch": paper_flops,
+                        "peak_source": "FP64 FMA throughput measured on this pool's GB300 (nominal "
+                                       "1.25 TFLOP/s); FP64 is ALU-bound here (~270 flop per 24 B/DOF)"}
     line["smoother"] = {"gdof_s": n / (ms * 1e-3) / 1e9, "ms_patch_sweep": ms,
-                        "note": "EA patch sweep alone (gather, 6 transforms, weighted scatter), FP64"}
+                        "note": ("EA" if fam == -1 else "FA (one direction)")
+                                + " patch sweep alone (gather, 6 transforms, weighted scatter), FP64"}
     # apply kernel (FP64): share of the solve
     ms_apply = time_kernel(lambda: h.apply(h.L, g, r), 10, stream, flush)
     line["apply"] = {"ms": ms_apply, "gdof_s": n / (ms_apply * 1e-3) / 1e9,

@@ -212,6 +212,11 @@ int pmg_schwarz_sweep(pmg_hier h, int level, int family, const double* r_dev, do
 const char* pmg_status_string(int status);
 const char* pmg_last_error(pmg_hier h);
 
+/* Multiply-adds one pmg_schwarz_sweep of (level, family) executes in its six
+ * eigenvector line passes, as implemented (even-odd split on centro-symmetric
+ * axes): the figure the benchmark's roofline uses.  Host only. */
+int pmg_schwarz_sweep_fma(pmg_hier h, int level, int family, double* fma);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all hierarchies, all devices); for counting launches in a timed region. */
 unsigned long long pmg_kernel_launches(void);

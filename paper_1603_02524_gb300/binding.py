@@ -25,7 +25,8 @@ EXPORTS = ["pmg_options_default", "pmg_grid_create", "pmg_grid_destroy", "pmg_gr
            "pmg_hierarchy_build", "pmg_hierarchy_destroy", "pmg_num_levels", "pmg_level_info",
            "pmg_apply", "pmg_residual", "pmg_rhs", "pmg_smooth", "pmg_restrict", "pmg_prolong",
            "pmg_coarse_solve", "pmg_vcycle", "pmg_solve", "pmg_solve_host", "pmg_status_string",
-           "pmg_last_error", "pmg_schwarz_sweep", "pmg_kernel_launches", "pmg_coarse_solve_static"]
+           "pmg_last_error", "pmg_schwarz_sweep", "pmg_kernel_launches", "pmg_coarse_solve_static",
+           "pmg_schwarz_sweep_fma"]
 
 
 class PmgOptions(ctypes.Structure):
@@ -84,6 +85,7 @@ def load(path: str | None = None):
         "pmg_schwarz_sweep": (i, [vp, i, i, vp, vp, vp]),
         "pmg_kernel_launches": (ctypes.c_ulonglong, []),
         "pmg_coarse_solve_static": (i, [vp, vp, vp, vp]),
+        "pmg_schwarz_sweep_fma": (i, [vp, i, i, ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -222,6 +224,11 @@ class Hierarchy:
         n = self.ndof(0)
         _check("pmg_coarse_solve", load().pmg_coarse_solve(self.handle, _dev(f0, n), _dev(u0, n),
                                                            _stream(stream)), self.handle)
+
+    def schwarz_sweep_fma(self, level, family):
+        out = ctypes.c_double()
+        _check("pmg_schwarz_sweep_fma", load().pmg_schwarz_sweep_fma(self.handle, level, family, ctypes.byref(out)))
+        return out.value
 
     def schwarz_sweep(self, level, family, r, u, stream=None):
         n = self.ndof(level)

@@ -5,10 +5,10 @@
 namespace pmg {
 
 int fdm_dispatch_d2(const LevelDims& dm, const FdmFamily<double>& fam, const double* r, double* u,
-                     double omega, cudaStream_t s) {
+                     cudaStream_t s) {
   const int na = fam.ax[0].n, nb = fam.ax[1].n, nc = fam.ax[2].n;
 #define C(A, B, CC) \
-  if (na == A && nb == B && nc == CC) return fdm_launch<double, A, B, CC>(dm, fam, r, u, omega, s);
+  if (na == A && nb == B && nc == CC) return fdm_launch<double, A, B, CC>(dm, fam, r, u, s);
   C(3, 3, 1) C(5, 5, 1) C(7, 7, 1) C(9, 9, 1) C(13, 13, 1) C(17, 17, 1) C(23, 23, 1)
   C(33, 33, 1) C(43, 43, 1)
   C(4, 3, 1) C(4, 5, 1) C(8, 5, 1) C(8, 7, 1) C(8, 9, 1) C(16, 9, 1) C(16, 13, 1)

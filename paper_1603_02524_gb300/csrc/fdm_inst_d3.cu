@@ -5,10 +5,10 @@
 namespace pmg {
 
 int fdm_dispatch_d3(const LevelDims& dm, const FdmFamily<double>& fam, const double* r, double* u,
-                     double omega, cudaStream_t s) {
+                     cudaStream_t s) {
   const int na = fam.ax[0].n, nb = fam.ax[1].n, nc = fam.ax[2].n;
 #define C(A, B, CC) \
-  if (na == A && nb == B && nc == CC) return fdm_launch<double, A, B, CC>(dm, fam, r, u, omega, s);
+  if (na == A && nb == B && nc == CC) return fdm_launch<double, A, B, CC>(dm, fam, r, u, s);
   C(3, 3, 3) C(5, 5, 5) C(7, 7, 7) C(9, 9, 9) C(13, 13, 13) C(17, 17, 17) C(23, 23, 23)
   C(4, 3, 3) C(4, 5, 5) C(8, 5, 5) C(8, 7, 7) C(8, 9, 9) C(16, 9, 9) C(16, 13, 13)
   C(32, 17, 17) C(32, 23, 23)

@@ -3,170 +3,292 @@
 // One CTA per subdomain.  The kernel serves both the element-centred (EA) and
 // the face-centred (FA) families: every patch is a tensor product of three
 // contiguous global 1-D index ranges (one per axis, wrapped on periodic axes,
-// truncated at Dirichlet walls), and every axis carries its own eigen-table
-// (S, lambda) of L_{s,d} S = M_{s,d} S Lambda and weight vector w.
+// truncated at Dirichlet walls), and every axis carries its own eigen-table of
+// L_{s,d} S = M_{s,d} S Lambda:
 //
 //   gather   r_s = R_s r                          (0 outside the domain)
 //   forward  t = (S_c^T (x) S_b^T (x) S_a^T) r_s   three in-place line passes
 //   scale    t /= lambda_a + lambda_b + lambda_c
-//   backward t = (S_c (x) S_b (x) S_a) t
-//   scatter  u += omega * (w_c (x) w_b (x) w_a) t   (atomic: patches overlap)
+//   backward t = (W_c (x) W_b (x) W_a) t,  W_q = diag(w_q) S_q (omega folded into W_a)
+//   scatter  u += t                               (atomic: patches overlap)
 //
 // Positions outside the domain carry a decoupled identity in the eigen-table
-// and weight 0, so the tensor algebra needs no special cases.  Each thread of
-// a line pass owns one whole line: it loads the line into registers, then
-// writes the transformed line back over the same shared-memory locations.
+// and weight 0, so the tensor algebra needs no special cases.
+//
+// Even-odd split: when the 1-D patch problem of an axis is centro-symmetric
+// (every interior patch of a uniform grid), its eigenvectors are symmetric or
+// antisymmetric.  The host then stores them folded (symmetric modes first), and
+// a line pass works on the half-sums v_a + v_{n-1-a} and half-differences
+// v_a - v_{n-1-a}, which roughly halves the multiply-adds of that pass.
 #pragma once
 
 #include "pmg_internal.h"
 
 namespace pmg {
 
-// In-place transform of the lines of `buf` along one axis of length N.
-// FORWARD: out_i = sum_a S[a][i] v_a  (S^T); else out_a = sum_i S[a][i] v_i.
-template <typename T, int N, bool FORWARD>
-__device__ __forceinline__ void line_pass(T* buf, const T* S, int nlines, int line_stride_lo,
-                                          int lo_count, int line_stride_hi, int stride) {
+constexpr long long kInvalidOffset = -(1LL << 60);
+
+// 16-byte vector of T (shared-memory table rows are padded to a multiple of it).
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  using type = float4;
+  static constexpr int W = 4;
+  __device__ static float get(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+};
+template <> struct Vec16<double> {
+  using type = double2;
+  static constexpr int W = 2;
+  __device__ static double get(const double2& v, int k) { return k == 0 ? v.x : v.y; }
+};
+template <typename T>
+__host__ __device__ constexpr int padded(int n) { return (n + Vec16<T>::W - 1) / Vec16<T>::W * Vec16<T>::W; }
+
+// acc[0..N) += row[0..N) * x, row 16-byte aligned and padded.
+template <typename T, int N>
+__device__ __forceinline__ void axpy_row(T* acc, const T* row, T x) {
+  using V = Vec16<T>;
+  const typename V::type* r = reinterpret_cast<const typename V::type*>(row);
+#pragma unroll
+  for (int c = 0; c < padded<T>(N) / V::W; ++c) {
+    const typename V::type s = r[c];
+#pragma unroll
+    for (int k = 0; k < V::W; ++k)
+      if (c * V::W + k < N) acc[c * V::W + k] = fma(V::get(s, k), x, acc[c * V::W + k]);
+  }
+}
+
+// General in-place line transform along an axis of length N: out_i = sum_a M[a][i] v_a,
+// M row-major with padded rows (forward: M = S, node-major; backward: M = W^T,
+// mode-major, so the same form applies W).  Each thread owns a line and keeps
+// all N partial sums in registers; long lines (N > 32) use dot products instead.
+template <typename T, int N>
+__device__ __forceinline__ void line_pass(T* buf, const T* M, int nlines, int lo_stride, int lo_count,
+                                          int hi_stride, int stride) {
+  constexpr int NP_ = padded<T>(N);
   for (int l = threadIdx.x; l < nlines; l += blockDim.x) {
-    const int base = (l % lo_count) * line_stride_lo + (l / lo_count) * line_stride_hi;
+    const int base = (l % lo_count) * lo_stride + (l / lo_count) * hi_stride;
     T v[N];
 #pragma unroll
     for (int a = 0; a < N; ++a) v[a] = buf[base + a * stride];
-#pragma unroll 1
-    for (int i = 0; i < N; ++i) {
-      T s = T(0);
+    if constexpr (N <= 32) {
+      T acc[N];
 #pragma unroll
-      for (int a = 0; a < N; ++a) s = fma(FORWARD ? S[a * N + i] : S[i * N + a], v[a], s);
-      buf[base + i * stride] = s;
+      for (int i = 0; i < N; ++i) acc[i] = T(0);
+#pragma unroll
+      for (int a = 0; a < N; ++a) axpy_row<T, N>(acc, M + a * NP_, v[a]);
+#pragma unroll
+      for (int i = 0; i < N; ++i) buf[base + i * stride] = acc[i];
+    } else {
+#pragma unroll 1
+      for (int i = 0; i < N; ++i) {
+        T s = T(0);
+#pragma unroll
+        for (int a = 0; a < N; ++a) s = fma(M[a * NP_ + i], v[a], s);
+        buf[base + i * stride] = s;
+      }
     }
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void atomic_add_t(T* p, T v) {
-  atomicAdd(p, v);
+// Even-odd line transform (centro-symmetric axis).  Shared-memory layout: the
+// symmetric block (NE rows, padded) then the antisymmetric block (NO rows,
+// padded); NE = N - N/2, NO = N/2.  Forward: rows = nodes 0..NE-1 / 0..NO-1 of
+// S, output modes symmetric first (positions 0..NE-1) then antisymmetric.
+// Backward: rows = modes of W^T (transposed backward table), output nodes.
+template <typename T, int N, bool FORWARD>
+__device__ __forceinline__ void line_pass_sym(T* buf, const T* M, int nlines, int lo_stride,
+                                              int lo_count, int hi_stride, int stride) {
+  constexpr int H = N / 2, NE = N - H, NO = H;
+  constexpr int PE = padded<T>(NE), PO = padded<T>(NO > 0 ? NO : 1);
+  const T* Me = M;
+  const T* Mo = M + NE * PE;
+  for (int l = threadIdx.x; l < nlines; l += blockDim.x) {
+    const int base = (l % lo_count) * lo_stride + (l / lo_count) * hi_stride;
+    T v[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) v[a] = buf[base + a * stride];
+    T ae[NE], ao[NO > 0 ? NO : 1];
+#pragma unroll
+    for (int i = 0; i < NE; ++i) ae[i] = T(0);
+#pragma unroll
+    for (int i = 0; i < NO; ++i) ao[i] = T(0);
+    if (FORWARD) {
+#pragma unroll
+      for (int a = 0; a < H; ++a) {
+        axpy_row<T, NE>(ae, Me + a * PE, v[a] + v[N - 1 - a]);
+        axpy_row<T, NO>(ao, Mo + a * PO, v[a] - v[N - 1 - a]);
+      }
+      if (NE > H) axpy_row<T, NE>(ae, Me + H * PE, v[H]);
+#pragma unroll
+      for (int i = 0; i < NE; ++i) buf[base + i * stride] = ae[i];
+#pragma unroll
+      for (int i = 0; i < NO; ++i) buf[base + (NE + i) * stride] = ao[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < NE; ++i) axpy_row<T, NE>(ae, Me + i * PE, v[i]);
+#pragma unroll
+      for (int i = 0; i < NO; ++i) axpy_row<T, NO>(ao, Mo + i * PO, v[NE + i]);
+#pragma unroll
+      for (int a = 0; a < H; ++a) {
+        buf[base + a * stride] = ae[a] + ao[a];
+        buf[base + (N - 1 - a) * stride] = ae[a] - ao[a];
+      }
+      if (NE > H) buf[base + H * stride] = ae[H];
+    }
+  }
 }
+
+template <typename T, int N, bool FORWARD>
+__device__ __forceinline__ void axis_pass(bool sym, T* buf, const T* M, int nlines, int lo_stride,
+                                          int lo_count, int hi_stride, int stride) {
+  if (N > 1 && N <= 32 && sym) line_pass_sym<T, N, FORWARD>(buf, M, nlines, lo_stride, lo_count, hi_stride, stride);
+  else line_pass<T, N>(buf, M, nlines, lo_stride, lo_count, hi_stride, stride);
+}
+
+// Copy an n x n table (general, row-major) or its even-odd folded blocks from
+// global memory into padded shared-memory rows.
+template <typename T, int N>
+__device__ __forceinline__ void load_table(T* dst, const T* src, bool sym) {
+  constexpr int NP_ = padded<T>(N);
+  constexpr int H = N / 2, NE = N - H, NO = H;
+  constexpr int PE = padded<T>(NE), PO = padded<T>(NO > 0 ? NO : 1);
+  if (sym && N > 1 && N <= 32) {
+    for (int t = threadIdx.x; t < NE * NE; t += blockDim.x) dst[(t / NE) * PE + t % NE] = src[t];
+    for (int t = threadIdx.x; t < NO * NO; t += blockDim.x)
+      dst[NE * PE + (t / NO) * PO + t % NO] = src[NE * NE + t];
+  } else {
+    for (int t = threadIdx.x; t < N * N; t += blockDim.x) dst[(t / N) * NP_ + t % N] = src[t];
+  }
+}
+
+// 1 / s: hardware single-precision reciprocal refined by Newton's iteration
+// x <- x (2 - s x), written as x <- x + x (1 - s x); each step squares the
+// relative error (2^-23 -> 2^-46 -> below double rounding).
+__device__ __forceinline__ double recip(double s) {
+  double x = (double)__frcp_rn((float)s);
+  double e = fma(-s, x, 1.0);
+  x = fma(x, e, x);
+  e = fma(-s, x, 1.0);
+  return fma(x, e, x);
+}
+__device__ __forceinline__ float recip(float s) { return __frcp_rn(s); }
 
 template <typename T, int NA, int NB, int NC>
 __global__ void __launch_bounds__(256)
-fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restrict__ u, T omega) {
+fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restrict__ u) {
   constexpr int NN = NA * NB * NC;
   extern __shared__ __align__(16) unsigned char fdm_smem[];
-  T* buf = reinterpret_cast<T*>(fdm_smem);
-  T* Sa = buf + NN;
-  T* Sb = Sa + NA * NA;
-  T* Sc = Sb + NB * NB;
-  T* la = Sc + NC * NC;
+  long long* off = reinterpret_cast<long long*>(fdm_smem);        // NA + NB + NC
+  T* buf = reinterpret_cast<T*>(off + (NA + NB + NC + 1) / 2 * 2);
+  T* Sq[3];
+  T* Wq[3];
+  Sq[0] = buf + padded<T>(NN);
+  Wq[0] = Sq[0] + NA * padded<T>(NA);
+  Sq[1] = Wq[0] + NA * padded<T>(NA);
+  Wq[1] = Sq[1] + NB * padded<T>(NB);
+  Sq[2] = Wq[1] + NB * padded<T>(NB);
+  Wq[2] = Sq[2] + NC * padded<T>(NC);
+  T* la = Wq[2] + NC * padded<T>(NC);
   T* lb = la + NA;
   T* lc = lb + NB;
-  T* wa = lc + NC;
-  T* wb = wa + NA;
-  T* wc = wb + NB;
 
   const int ca = fam.ax[0].count, cb = fam.ax[1].count;
   const int pid = blockIdx.x;
-  const int pa = pid % ca, pb = (pid / ca) % cb, pc = pid / (ca * cb);
-  const int pidx[3] = {pa, pb, pc};
+  const int pidx[3] = {pid % ca, (pid / ca) % cb, pid / (ca * cb)};
+  const int nq[3] = {NA, NB, NC};
+  T* lq[3] = {la, lb, lc};
+  bool sym[3];
+  const long long nodes_el = (long long)dm.NP * dm.NP * dm.NPz;
+  const long long estride[3] = {nodes_el, nodes_el * dm.ne[0], nodes_el * dm.ne[0] * dm.ne[1]};
+  const long long nstride[3] = {1, dm.NP, (long long)dm.NP * dm.NP};
+  long long* offq[3] = {off, off + NA, off + NA + NB};
 
-  // eigen-tables and weights of this patch
-  {
-    const T* gS[3] = {fam.ax[0].S + (size_t)pa * NA * NA, fam.ax[1].S + (size_t)pb * NB * NB,
-                      fam.ax[2].S + (size_t)pc * NC * NC};
-    for (int t = threadIdx.x; t < NA * NA; t += blockDim.x) Sa[t] = gS[0][t];
-    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) Sb[t] = gS[1][t];
-    for (int t = threadIdx.x; t < NC * NC; t += blockDim.x) Sc[t] = gS[2][t];
-    if (threadIdx.x < NA) {
-      la[threadIdx.x] = fam.ax[0].lam[(size_t)pa * NA + threadIdx.x];
-      wa[threadIdx.x] = fam.ax[0].w[(size_t)pa * NA + threadIdx.x];
-    }
-    if (threadIdx.x < NB) {
-      lb[threadIdx.x] = fam.ax[1].lam[(size_t)pb * NB + threadIdx.x];
-      wb[threadIdx.x] = fam.ax[1].w[(size_t)pb * NB + threadIdx.x];
-    }
-    if (threadIdx.x < NC) {
-      lc[threadIdx.x] = fam.ax[2].lam[(size_t)pc * NC + threadIdx.x];
-      wc[threadIdx.x] = fam.ax[2].w[(size_t)pc * NC + threadIdx.x];
-    }
-  }
-
-  // per buffer axis: first global 1-D index, size, node count of the physical axis
-  int start[3], gN[3], npp[3], phys[3], per[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    phys[q] = fam.ax[q].phys;
-    npp[q] = (phys[q] == 2) ? dm.NPz : dm.NP;
-    start[q] = fam.ax[q].start0 + pidx[q] * npp[q];
-    gN[q] = fam.ax[q].N;
-    per[q] = fam.ax[q].periodic;
-  }
-  const long long nodes_el = (long long)dm.NP * dm.NP * dm.NPz;
-
-  // element-major offset of buffer position (a, b, c), or -1 outside the domain
-  auto offset = [&](int a, int b, int c) -> long long {
-    const int loc[3] = {a, b, c};
-    int X[3] = {0, 0, 0};
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      int G = start[q] + loc[q];
-      if (per[q]) {
-        G %= gN[q];
-        if (G < 0) G += gN[q];
-      } else if (G < 0 || G >= gN[q]) {
-        return -1;
-      }
-      X[phys[q]] = G;
+    const FdmAxis<T>& ax = fam.ax[q];
+    const int n = nq[q];
+    const size_t p = pidx[q];
+    sym[q] = ax.sym[p] != 0;
+    if (q == 0) {
+      load_table<T, NA>(Sq[0], ax.S + p * n * n, sym[0]);
+      load_table<T, NA>(Wq[0], ax.W + p * n * n, sym[0]);
+    } else if (q == 1) {
+      load_table<T, NB>(Sq[1], ax.S + p * n * n, sym[1]);
+      load_table<T, NB>(Wq[1], ax.W + p * n * n, sym[1]);
+    } else {
+      load_table<T, NC>(Sq[2], ax.S + p * n * n, sym[2]);
+      load_table<T, NC>(Wq[2], ax.W + p * n * n, sym[2]);
     }
-    const int NP = dm.NP;
-    const int ex = X[0] / NP, i = X[0] % NP, ey = X[1] / NP, j = X[1] % NP;
-    const int ez = X[2] / dm.NPz, k = X[2] % dm.NPz;
-    return (((long long)ez * dm.ne[1] + ey) * dm.ne[0] + ex) * nodes_el + ((long long)k * NP + j) * NP + i;
-  };
+    if (threadIdx.x < n) {
+      const int a = threadIdx.x;
+      lq[q][a] = ax.lam[p * n + a];
+      // element-major offset contribution of local index a, or "invalid"
+      const int ph = ax.phys;
+      const int npp = (ph == 2) ? dm.NPz : dm.NP;
+      int G = ax.start0 + (int)p * npp + a;
+      long long o;
+      if (ax.periodic) {
+        G %= ax.N;
+        if (G < 0) G += ax.N;
+        o = (long long)(G / npp) * estride[ph] + (G % npp) * nstride[ph];
+      } else if (G < 0 || G >= ax.N) {
+        o = kInvalidOffset;
+      } else {
+        o = (long long)(G / npp) * estride[ph] + (G % npp) * nstride[ph];
+      }
+      offq[q][a] = o;
+    }
+  }
+  __syncthreads();
 
   for (int t = threadIdx.x; t < NN; t += blockDim.x) {
     const int a = t % NA, b = (t / NA) % NB, c = t / (NA * NB);
-    const long long o = offset(a, b, c);
+    const long long o = off[a] + off[NA + b] + off[NA + NB + c];
     buf[t] = o >= 0 ? r[o] : T(0);
   }
   __syncthreads();
 
   // forward transforms
-  line_pass<T, NA, true>(buf, Sa, NB * NC, NA, NB * NC, 0, 1);
+  axis_pass<T, NA, true>(sym[0], buf, Sq[0], NB * NC, NA, NB * NC, 0, 1);
   __syncthreads();
-  line_pass<T, NB, true>(buf, Sb, NA * NC, 1, NA, NA * NB, NA);
+  axis_pass<T, NB, true>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA);
   __syncthreads();
   if (NC > 1) {
-    line_pass<T, NC, true>(buf, Sc, NA * NB, 1, NA * NB, 0, NA * NB);
+    axis_pass<T, NC, true>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB);
     __syncthreads();
   }
   for (int t = threadIdx.x; t < NN; t += blockDim.x) {
     const int a = t % NA, b = (t / NA) % NB, c = t / (NA * NB);
-    buf[t] = buf[t] / (la[a] + lb[b] + lc[c]);
+    buf[t] *= recip(la[a] + lb[b] + lc[c]);
   }
   __syncthreads();
   if (NC > 1) {
-    line_pass<T, NC, false>(buf, Sc, NA * NB, 1, NA * NB, 0, NA * NB);
+    axis_pass<T, NC, false>(sym[2], buf, Wq[2], NA * NB, 1, NA * NB, 0, NA * NB);
     __syncthreads();
   }
-  line_pass<T, NB, false>(buf, Sb, NA * NC, 1, NA, NA * NB, NA);
+  axis_pass<T, NB, false>(sym[1], buf, Wq[1], NA * NC, 1, NA, NA * NB, NA);
   __syncthreads();
-  line_pass<T, NA, false>(buf, Sa, NB * NC, NA, NB * NC, 0, 1);
+  axis_pass<T, NA, false>(sym[0], buf, Wq[0], NB * NC, NA, NB * NC, 0, 1);
   __syncthreads();
 
   for (int t = threadIdx.x; t < NN; t += blockDim.x) {
     const int a = t % NA, b = (t / NA) % NB, c = t / (NA * NB);
-    const T wt = wa[a] * wb[b] * wc[c];
-    if (wt != T(0)) {
-      const long long o = offset(a, b, c);
-      if (o >= 0) atomic_add_t(u + o, omega * wt * buf[t]);
-    }
+    const long long o = off[a] + off[NA + b] + off[NA + NB + c];
+    if (o >= 0) atomicAdd(u + o, buf[t]);
   }
 }
 
 template <typename T, int NA, int NB, int NC>
-int fdm_launch(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, T omega,
-               cudaStream_t s) {
-  const size_t smem =
-      sizeof(T) * ((size_t)NA * NB * NC + NA * NA + NB * NB + NC * NC + 2 * (NA + NB + NC));
+constexpr size_t fdm_smem_bytes() {
+  return sizeof(long long) * ((NA + NB + NC + 1) / 2 * 2) +
+         sizeof(T) * ((size_t)padded<T>(NA * NB * NC) +
+                      2 * (NA * padded<T>(NA) + NB * padded<T>(NB) + NC * padded<T>(NC)) + NA + NB + NC);
+}
+
+template <typename T, int NA, int NB, int NC>
+int fdm_launch(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, cudaStream_t s) {
+  constexpr size_t smem = fdm_smem_bytes<T, NA, NB, NC>();
+  static_assert(smem <= 227 * 1024, "patch does not fit in shared memory");
   static bool attr_done = false;
   if (!attr_done && smem > 48 * 1024) {
     if (cudaFuncSetAttribute(fdm_kernel<T, NA, NB, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -175,7 +297,8 @@ int fdm_launch(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, T
   }
   attr_done = true;
   if (fam.count_total <= 0) return PMG_OK;
-  count_launch(); fdm_kernel<T, NA, NB, NC><<<fam.count_total, 256, smem, s>>>(dm, fam, r, u, omega);
+  count_launch();
+  fdm_kernel<T, NA, NB, NC><<<fam.count_total, 256, smem, s>>>(dm, fam, r, u);
   return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
 }
 

@@ -6,6 +6,8 @@
 // Algorithm 2 vector steps).
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "pmg_internal.h"
 
 namespace pmg {
@@ -68,33 +70,64 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const T* __restrict__ u, const T* 
   }
   T* sel = su + el * S::NODES;
   T* ael = acc + el * S::NODES;
+  constexpr int H = NP / 2, NE = NP - H, NO = H;
 #pragma unroll 1
   for (int d = 0; d < DIM; ++d) {
     if (active) {
-      int off, stride, ia = 0, ib = 0, oa = 0, ob = 0;   // (ia on axis oa, ib on axis ob) = line coords
+      int off, stride;
       if (DIM == 3) {
-        if (d == 0) { off = line * NP; stride = 1; ia = line % NP; oa = 1; ib = line / NP; ob = 2; }
-        else if (d == 1) { ia = line % NP; ib = line / NP; off = ib * NP * NP + ia; stride = NP; oa = 0; ob = 2; }
-        else { ia = line % NP; ib = line / NP; off = ib * NP + ia; stride = NP * NP; oa = 0; ob = 1; }
+        if (d == 0) { off = line * NP; stride = 1; }
+        else if (d == 1) { off = (line / NP) * NP * NP + line % NP; stride = NP; }
+        else { off = line; stride = NP * NP; }
       } else {
-        if (d == 0) { off = line * NP; stride = 1; ia = line; oa = 1; }
-        else { off = line; stride = NP; ia = line; oa = 0; }
+        if (d == 0) { off = line * NP; stride = 1; }
+        else { off = line; stride = NP; }
       }
       T x[NP], y[NP];
 #pragma unroll
       for (int a = 0; a < NP; ++a) x[a] = sel[off + a * stride];
       const T* L0 = at.L0[d] + (size_t)me[d] * NP * NP;
+      if (__ldg(at.sym[d] + me[d])) {
+        // even-odd split of the centro-symmetric block (folded table layout)
+        T xp[NE], xm[NO > 0 ? NO : 1];
 #pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        T s = T(0);
+        for (int a = 0; a < H; ++a) {
+          xp[a] = x[a] + x[P - a];
+          xm[a] = x[a] - x[P - a];
+        }
+        if (NE > H) xp[NE - 1] = x[H];
+        const T* E = L0;
+        const T* O = L0 + NE * NE;
 #pragma unroll
-        for (int a = 0; a < NP; ++a) s = fma(__ldg(L0 + i * NP + a), x[a], s);
-        y[i] = s;
+        for (int i = 0; i < H; ++i) {
+          T e = T(0), o = T(0);
+#pragma unroll
+          for (int a = 0; a < NE; ++a) e = fma(__ldg(E + i * NE + a), xp[a], e);
+#pragma unroll
+          for (int a = 0; a < NO; ++a) o = fma(__ldg(O + i * NO + a), xm[a], o);
+          y[i] = e + o;
+          y[P - i] = e - o;
+        }
+        if (NE > H) {
+          T e = T(0);
+#pragma unroll
+          for (int a = 0; a < NE; ++a) e = fma(__ldg(E + H * NE + a), xp[a], e);
+          y[H] = e;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          T s = T(0);
+#pragma unroll
+          for (int a = 0; a < NP; ++a) s = fma(__ldg(L0 + i * NP + a), x[a], s);
+          y[i] = s;
+        }
       }
-      const T* c = at.cpl[d] + (size_t)me[d] * 8;
+      // neighbour blocks L^-, L^+ (rank <= 3, already scaled by M_d^-1)
+      const T* c = at.cpl[d] + (size_t)me[d] * (2 * NP + 8);
       const long long estride = (d == 0) ? 1 : (d == 1 ? (long long)dm.ne[0] : (long long)dm.ne[0] * dm.ne[1]);
       const int ned = dm.ne[d];
-      if (__ldg(c + 3) != T(0)) {          // neighbour m-1 exists
+      if (__ldg(c + 2 * NP + 2) != T(0)) {          // neighbour m-1 exists
         long long en = (me[d] > 0) ? e - estride : e + (long long)(ned - 1) * estride;
         const T* un = u + en * S::NODES + off;
         T uP = T(0), dP = T(0);
@@ -104,12 +137,11 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const T* __restrict__ u, const T* 
           dP = fma(__ldg(at.DP + a), val, dP);
           if (a == P) uP = val;
         }
-        const T aL = __ldg(c + 0), bL = __ldg(c + 1), cL = __ldg(c + 2);
 #pragma unroll
-        for (int i = 0; i < NP; ++i) y[i] = fma(-aL * __ldg(at.D0 + i), uP, y[i]);
-        y[0] += bL * dP - cL * uP;
+        for (int i = 0; i < NP; ++i) y[i] = fma(__ldg(c + i), uP, y[i]);
+        y[0] += __ldg(c + 2 * NP + 0) * dP - __ldg(c + 2 * NP + 1) * uP;
       }
-      if (__ldg(c + 7) != T(0)) {          // neighbour m+1 exists
+      if (__ldg(c + 2 * NP + 5) != T(0)) {          // neighbour m+1 exists
         long long en = (me[d] < ned - 1) ? e + estride : e - (long long)(ned - 1) * estride;
         const T* un = u + en * S::NODES + off;
         T u0 = T(0), d0 = T(0);
@@ -119,25 +151,34 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const T* __restrict__ u, const T* 
           d0 = fma(__ldg(at.D0 + a), val, d0);
           if (a == 0) u0 = val;
         }
-        const T aR = __ldg(c + 4), bR = __ldg(c + 5), cR = __ldg(c + 6);
 #pragma unroll
-        for (int i = 0; i < NP; ++i) y[i] = fma(aR * __ldg(at.DP + i), u0, y[i]);
-        y[P] -= bR * d0 + cR * u0;
+        for (int i = 0; i < NP; ++i) y[i] = fma(__ldg(c + NP + i), u0, y[i]);
+        y[P] -= __ldg(c + 2 * NP + 3) * d0 + __ldg(c + 2 * NP + 4) * u0;
       }
-      T scale = __ldg(at.M[oa] + (size_t)me[oa] * NP + ia);
-      if (DIM == 3) scale *= __ldg(at.M[ob] + (size_t)me[ob] * NP + ib);
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
-        T val = scale * y[i];
-        if (d == 0) ael[off + i * stride] = val;
-        else ael[off + i * stride] += val;
+        if (d == 0) ael[off + i * stride] = y[i];
+        else ael[off + i * stride] += y[i];
       }
     }
     __syncthreads();
   }
+  // v = (M_z (x) M_y (x) M_x) * (sum over axes of M_d^-1 L_d u)
   for (int t = tid; t < nodes_blk; t += blockDim.x) {
     long long g = e0 * S::NODES + t;
-    if (g < total) v[g] = RESIDUAL ? f[g] - acc[t] : acc[t];
+    if (g >= total) continue;
+    const long long ee = g / S::NODES;
+    const int nd = (int)(g % S::NODES);
+    const int i = nd % NP, j = (nd / NP) % NP;
+    const int mx = (int)(ee % dm.ne[0]), my = (int)((ee / dm.ne[0]) % dm.ne[1]);
+    T m = __ldg(at.M[0] + (size_t)mx * NP + i) * __ldg(at.M[1] + (size_t)my * NP + j);
+    if (DIM == 3) {
+      const int k = nd / (NP * NP);
+      const int mz = (int)(ee / ((long long)dm.ne[0] * dm.ne[1]));
+      m *= __ldg(at.M[2] + (size_t)mz * NP + k);
+    }
+    const T val = m * acc[t];
+    v[g] = RESIDUAL ? f[g] - val : val;
   }
 }
 
@@ -315,60 +356,88 @@ __device__ __forceinline__ long long coarse_off(const LevelDims& dm, int X, int 
   return (((long long)ez * dm.ne[1] + ey) * dm.ne[0] + ex) * 8 + (k * 2 + j) * 2 + i;
 }
 
-__global__ void coarse_axis_kernel(LevelDims dm, int axis, int transpose, const double* __restrict__ S,
-                                   int N, const double* __restrict__ in, double* __restrict__ out) {
+// One axis transform of the coarse solve, grid-stride over all outputs.
+__device__ __forceinline__ void coarse_axis_pass(const LevelDims& dm, int axis, bool transpose,
+                                                 const double* __restrict__ S, int N,
+                                                 const double* in, double* out) {
   const int NX = dm.ne[0] * 2, NY = dm.ne[1] * 2, NZ = (dm.dim == 3) ? dm.ne[2] * 2 : 1;
   const long long total = (long long)NX * NY * NZ;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    int X = (int)(t % NX), Y = (int)((t / NX) % NY), Z = (int)(t / ((long long)NX * NY));
-    int o = axis == 0 ? X : (axis == 1 ? Y : Z);
+    const int X = (int)(t % NX), Y = (int)((t / NX) % NY), Z = (int)(t / ((long long)NX * NY));
+    const int o = axis == 0 ? X : (axis == 1 ? Y : Z);
     double s = 0.0;
+#pragma unroll 8
     for (int a = 0; a < N; ++a) {
-      int XX = axis == 0 ? a : X, YY = axis == 1 ? a : Y, ZZ = axis == 2 ? a : Z;
-      double m = transpose ? S[(size_t)a * N + o] : S[(size_t)o * N + a];
+      const int XX = axis == 0 ? a : X, YY = axis == 1 ? a : Y, ZZ = axis == 2 ? a : Z;
+      const double m = transpose ? S[(size_t)a * N + o] : S[(size_t)o * N + a];
       s = fma(m, in[coarse_off(dm, XX, YY, ZZ)], s);
     }
     out[coarse_off(dm, X, Y, Z)] = s;
   }
 }
 
-__global__ void coarse_scale_kernel(LevelDims dm, const double* __restrict__ lx,
-                                    const double* __restrict__ ly, const double* __restrict__ lz,
-                                    double tol, double* __restrict__ x) {
-  const int NX = dm.ne[0] * 2, NY = dm.ne[1] * 2, NZ = (dm.dim == 3) ? dm.ne[2] * 2 : 1;
-  const long long total = (long long)NX * NY * NZ;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    int X = (int)(t % NX), Y = (int)((t / NX) % NY), Z = (int)(t / ((long long)NX * NY));
-    double l = lx[X] + ly[Y] + (dm.dim == 3 ? lz[Z] : 0.0);
-    long long o = coarse_off(dm, X, Y, Z);
-    x[o] = (l > tol) ? x[o] / l : 0.0;
+// The whole coarse solve in one cooperative launch: forward transforms along
+// each axis, scale by the eigenvalue sums, backward transforms; grid-wide
+// synchronisation between the passes replaces seven separate launches.
+__global__ void __launch_bounds__(256)
+coarse_fdm_fused_kernel(LevelDims dm, CoarseFdm c, const double* f, double* u, double tol) {
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  const double* src = f;
+  int cur = 0;
+  for (int d = 0; d < dm.dim; ++d) {
+    coarse_axis_pass(dm, d, true, c.S[d], c.N[d], src, c.tmp[cur]);
+    grid.sync();
+    src = c.tmp[cur];
+    cur ^= 1;
+  }
+  {
+    const int NX = dm.ne[0] * 2, NY = dm.ne[1] * 2, NZ = (dm.dim == 3) ? dm.ne[2] * 2 : 1;
+    const long long total = (long long)NX * NY * NZ;
+    double* x = c.tmp[cur ^ 1];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+      const int X = (int)(t % NX), Y = (int)((t / NX) % NY), Z = (int)(t / ((long long)NX * NY));
+      const double l = c.lam[0][X] + c.lam[1][Y] + (dm.dim == 3 ? c.lam[2][Z] : 0.0);
+      const long long o = coarse_off(dm, X, Y, Z);
+      x[o] = (l > tol) ? x[o] / l : 0.0;
+    }
+    grid.sync();
+  }
+  for (int d = dm.dim - 1; d >= 0; --d) {
+    double* dst = (d == 0) ? u : c.tmp[cur];
+    coarse_axis_pass(dm, d, false, c.S[d], c.N[d], src, dst);
+    if (d > 0) grid.sync();
+    src = dst;
+    cur ^= 1;
   }
 }
 
 int launch_coarse_fdm(const LevelDims& dm, const CoarseFdm& c, const double* f, double* u,
                       cudaStream_t s) {
-  long long total = dm.ndof;
-  unsigned blocks = (unsigned)((total + 255) / 256);
-  if (blocks > 4096) blocks = 4096;
-  const double* src = f;
-  double* bufs[2] = {c.tmp[0], c.tmp[1]};
-  int cur = 0;
-  for (int d = 0; d < dm.dim; ++d) {          // forward: S_d^T along each axis
-    count_launch(); coarse_axis_kernel<<<blocks, 256, 0, s>>>(dm, d, 1, c.S[d], c.N[d], src, bufs[cur]);
-    src = bufs[cur];
-    cur ^= 1;
+  static int per_sm = -1, nsm = 0;
+  if (per_sm < 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_fdm_fused_kernel, 256, 0) !=
+            cudaSuccess)
+      return PMG_ECUDA;
   }
-  count_launch(); coarse_scale_kernel<<<blocks, 256, 0, s>>>(dm, c.lam[0], c.lam[1], dm.dim == 3 ? c.lam[2] : c.lam[0],
-                                             1e-13 * c.lam_max, bufs[cur ^ 1]);
-  for (int d = dm.dim - 1; d >= 0; --d) {     // backward: S_d
-    double* dst = (d == 0) ? u : bufs[cur];
-    count_launch(); coarse_axis_kernel<<<blocks, 256, 0, s>>>(dm, d, 0, c.S[d], c.N[d], src, dst);
-    src = dst;
-    cur ^= 1;
-  }
-  return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
+  long long want = (dm.ndof + 255) / 256;
+  long long cap = (long long)per_sm * nsm;
+  int blocks = (int)(want < cap ? want : cap);
+  if (blocks < 1) blocks = 1;
+  LevelDims dmv = dm;
+  CoarseFdm cv = c;
+  double tol = 1e-13 * c.lam_max;
+  const double* fv = f;
+  double* uv = u;
+  void* args[] = {&dmv, &cv, &fv, &uv, &tol};
+  count_launch();
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)coarse_fdm_fused_kernel, dim3(blocks),
+                                              dim3(256), args, 0, s);
+  return e == cudaSuccess ? PMG_OK : PMG_ECUDA;
 }
 
 // ---------------------------------------------------------------------------

@@ -51,12 +51,20 @@ struct Axis1DHost {
 // ---------------------------------------------------------------------------
 template <typename T>
 struct ApplyTables {
-  const T* L0[3];     // [Ne_d][NP][NP]
-  const T* M[3];      // [Ne_d][NP]
-  const T* cpl[3];    // [Ne_d][8]
+  // Per axis d and element index m along d:
+  const T* L0[3];     // [Ne_d][NP*NP]  M_d^-1 L^0 (row-scaled); even-odd folded when sym
+  const int* sym[3];  // [Ne_d]         1: M^-1 L^0 is centro-symmetric (folded form)
+  const T* M[3];      // [Ne_d][NP]     diagonal mass M_d
+  const T* cpl[3];    // [Ne_d][2NP+8]  neighbour coupling, scaled by M_d^-1 (see setup)
   const T* D0;        // D_{0,k}
   const T* DP;        // D_{P,k}
 };
+// Host-side apply tables of one axis (built from Axis1DHost by apply_axis_tables).
+struct ApplyAxisHost {
+  std::vector<double> L0, cpl;
+  std::vector<int> sym;
+};
+void apply_axis_tables(const Axis1DHost& a, ApplyAxisHost& t);
 
 // One axis of a family of patches (EA, or FA with this axis normal/lateral).
 template <typename T>
@@ -67,9 +75,10 @@ struct FdmAxis {
   int N;          // global 1-D size Ne * NP (1 for the trivial z axis in 2-D)
   int periodic;
   int phys;       // physical axis (0 x, 1 y, 2 z) this patch-buffer axis maps to
-  const T* S;     // [count][n][n]  S[p][a][i]: node a, mode i
-  const T* lam;   // [count][n]
-  const T* w;     // [count][n]
+  const T* S;     // [count][n*n] forward table S[p][a][i]: node a, mode i
+  const T* W;     // [count][n*n] backward table (diag(w) S)^T, mode-major (times omega on axis 0)
+  const T* lam;   // [count][n] eigenvalues in mode order
+  const int* sym; // [count] 1: centro-symmetric, tables stored in even-odd folded form
 };
 
 template <typename T>
@@ -105,6 +114,13 @@ struct CoarseFdm {            // exact global fast-diagonalisation solve at P = 
   double lam_max;
 };
 
+// host patch tables along one axis (see FdmAxis): S, W^T, lambda, symmetry flags
+struct AxisTables {
+  int n = 0, count = 0, start0 = 0;
+  std::vector<double> S, W, lam;
+  std::vector<int> sym;
+};
+
 struct Grid {
   int dim = 3, P = 1, bc_periodic = 0;
   int ne[3] = {1, 1, 1};
@@ -127,6 +143,8 @@ struct Hier {
   double* J64[kMaxLevels] = {};
   float* J32[kMaxLevels] = {};
   CoarseFdm coarse{};
+  // host copies of the patch-table shapes and symmetry flags (S/W/lam cleared)
+  std::vector<AxisTables> ec_shape[kMaxLevels], fc_shape[kMaxLevels];
   // MGCG work vectors (fine level, fp64)
   double *r = nullptr, *r_old = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;
   double* scal = nullptr;          // device scalars
@@ -138,6 +156,14 @@ struct Hier {
   std::vector<void*> owned;
   std::string err;
   int nsm = 152;
+  // CUDA graph of the MGCG preconditioner (V-cycle r -> z on the fixed work
+  // vectors), captured on first reuse on a private stream, replayed on the
+  // caller's stream; state 0 = not yet, 1 = captured, -1 = capture unsupported
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t pc_exec = nullptr;
+  int pc_state = 0;
+  int pc_calls = 0;
+  unsigned long long pc_launches = 0;
 };
 
 // scalar slots
@@ -155,11 +181,8 @@ void lagrange_matrix(const std::vector<double>& nodes, const std::vector<double>
 int sym_eig_jacobi(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& lam);
 int overlap_nodes(int P_l, int policy);
 double transition(double x, int weighting);
-// patch tables along one axis: n, count, start0, and S/lam/w host arrays
-void ec_axis_tables(const Axis1DHost& a, int No, int weighting, int& n, int& count, int& start0,
-                    std::vector<double>& S, std::vector<double>& lam, std::vector<double>& w);
-void fc_axis_tables(const Axis1DHost& a, int weighting, int& n, int& count, int& start0,
-                    std::vector<double>& S, std::vector<double>& lam, std::vector<double>& w);
+void ec_axis_tables(const Axis1DHost& a, int No, int weighting, AxisTables& t);
+void fc_axis_tables(const Axis1DHost& a, int weighting, AxisTables& t);
 void global_axis_eig(const Axis1DHost& a, std::vector<double>& S, std::vector<double>& lam);
 
 // ----------------------------------------------------------------------------
@@ -169,8 +192,7 @@ template <typename T>
 int launch_apply(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f, T* v,
                  cudaStream_t s);
 template <typename T>
-int launch_fdm(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, T omega,
-               cudaStream_t s);
+int launch_fdm(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, cudaStream_t s);
 template <typename T>
 int launch_restrict(const LevelDims& fine, const LevelDims& coarse, const T* J, const T* rf, T* fc,
                     cudaStream_t s);

@@ -306,34 +306,128 @@ double transition(double x, int weighting) {
   return x * (15.0 + x2 * (-10.0 + 3.0 * x2)) / 8.0;
 }
 
-// Generalised eigen-pairs of one patch axis with a decoupled identity for
-// positions outside the domain (Dirichlet truncation): S^T M S = I.
-static void patch_eig(const Axis1DHost& a, const std::vector<int>& gidx, double* S, double* lam) {
-  int n = (int)gidx.size();
-  std::vector<double> B((size_t)n * n, 0.0), Msq(n, 1.0);
+// Scaled 1-D patch matrix B = M^-1/2 L_s M^-1/2 with a decoupled identity for
+// positions outside the domain (Dirichlet truncation); Msq = diag(M)^1/2.
+static void patch_matrix(const Axis1DHost& a, const std::vector<int>& gidx, std::vector<double>& B,
+                         std::vector<double>& Msq) {
+  const int n = (int)gidx.size();
+  B.assign((size_t)n * n, 0.0);
+  Msq.assign(n, 1.0);
   for (int p = 0; p < n; ++p) Msq[p] = gidx[p] >= 0 ? std::sqrt(a.M[gidx[p]]) : 1.0;
   for (int p = 0; p < n; ++p)
     for (int q = 0; q < n; ++q) {
-      double v;
-      if (gidx[p] < 0 || gidx[q] < 0) {
-        v = (p == q) ? 1.0 : 0.0;
-      } else {
-        v = a.entry(gidx[p], gidx[q]);
-      }
+      double v = (gidx[p] < 0 || gidx[q] < 0) ? (p == q ? 1.0 : 0.0) : a.entry(gidx[p], gidx[q]);
       B[(size_t)p * n + q] = v / (Msq[p] * Msq[q]);
     }
-  // exact symmetry before Jacobi
-  for (int p = 0; p < n; ++p)
+  for (int p = 0; p < n; ++p)          // exact symmetry before the eigen-solver
     for (int q = p + 1; q < n; ++q) {
       double s = 0.5 * (B[(size_t)p * n + q] + B[(size_t)q * n + p]);
       B[(size_t)p * n + q] = s;
       B[(size_t)q * n + p] = s;
     }
-  std::vector<double> V, l;
-  if (sym_eig_jacobi(n, B, V, l) < 0) throw std::runtime_error("Jacobi eigen-solver did not converge");
-  for (int p = 0; p < n; ++p)
-    for (int i = 0; i < n; ++i) S[(size_t)p * n + i] = V[(size_t)p * n + i] / Msq[p];
-  for (int i = 0; i < n; ++i) lam[i] = l[i];
+}
+
+static void jacobi_or_throw(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& l) {
+  if (sym_eig_jacobi(n, A, V, l) < 0) throw std::runtime_error("Jacobi eigen-solver did not converge");
+}
+
+// Is the patch centro-symmetric: every position inside the domain, and B, M and
+// the weights unchanged under the reversal a -> n-1-a?
+static bool centro_symmetric(const std::vector<int>& gidx, const std::vector<double>& B,
+                             const std::vector<double>& Msq, const std::vector<double>& w) {
+  const int n = (int)gidx.size();
+  if (n < 2 || n > 32) return false;     // the kernel folds lines of at most 32 nodes
+  double big = 0.0;
+  for (double x : B) big = std::max(big, std::fabs(x));
+  for (int p = 0; p < n; ++p) {
+    if (gidx[p] < 0) return false;
+    if (std::fabs(Msq[p] - Msq[n - 1 - p]) > 1e-14 * Msq[p]) return false;
+    if (std::fabs(w[p] - w[n - 1 - p]) > 1e-15) return false;
+    for (int q = 0; q < n; ++q)
+      if (std::fabs(B[(size_t)p * n + q] - B[(size_t)(n - 1 - p) * n + (n - 1 - q)]) > 1e-13 * big)
+        return false;
+  }
+  return true;
+}
+
+// Eigen-tables of one patch axis (fast diagonalisation, Sec. 3.1):
+// L_s S = M_s S Lambda with S^T M_s S = I, forward table S, backward table
+// W = diag(w) S stored transposed.  General form: S row-major n x n (node,
+// mode), W^T row-major (mode, node), modes by ascending lambda.
+// Centro-symmetric form (sym = 1, n <= 32): the problem splits into the
+// symmetric and antisymmetric subspaces, solved separately; S holds the
+// symmetric block (NE x NE, rows = nodes 0..NE-1) then the antisymmetric one
+// (NO x NO, rows = nodes 0..NO-1); W^T the same blocks transposed (rows =
+// modes); lambda in the same mode order.
+static void patch_tables(const Axis1DHost& a, const std::vector<int>& gidx, const std::vector<double>& w,
+                         double* S, double* W, double* lam, int* sym) {
+  const int n = (int)gidx.size();
+  std::vector<double> B, Msq;
+  patch_matrix(a, gidx, B, Msq);
+  if (!centro_symmetric(gidx, B, Msq, w)) {
+    std::vector<double> V, l;
+    jacobi_or_throw(n, B, V, l);
+    for (int p = 0; p < n; ++p)
+      for (int i = 0; i < n; ++i) {
+        S[(size_t)p * n + i] = V[(size_t)p * n + i] / Msq[p];
+        W[(size_t)i * n + p] = w[p] * S[(size_t)p * n + i];     // W^T: mode-major
+      }
+    for (int i = 0; i < n; ++i) lam[i] = l[i];
+    *sym = 0;
+    return;
+  }
+  const int H = n / 2, NE = n - H, NO = H;
+  const double r2 = std::sqrt(0.5);
+  // reduced matrices in the bases e_k = (d_k + d_{n-1-k})/sqrt2 (k < H), e_mid = d_H,
+  // and o_k = (d_k - d_{n-1-k})/sqrt2
+  std::vector<double> Be((size_t)NE * NE), Bo((size_t)NO * NO);
+  auto Bat = [&](int p, int q) { return B[(size_t)p * n + q]; };
+  for (int k = 0; k < NE; ++k)
+    for (int l = 0; l < NE; ++l) {
+      double v;
+      if (k < H && l < H) v = Bat(k, l) + Bat(k, n - 1 - l);      // (1/2)(2 B_kl + 2 B_k,n-1-l)
+      else if (k < H) v = (Bat(k, H) + Bat(n - 1 - k, H)) * r2;
+      else if (l < H) v = (Bat(H, l) + Bat(H, n - 1 - l)) * r2;
+      else v = Bat(H, H);
+      Be[(size_t)k * NE + l] = v;
+    }
+  for (int k = 0; k < NO; ++k)
+    for (int l = 0; l < NO; ++l) Bo[(size_t)k * NO + l] = Bat(k, l) - Bat(k, n - 1 - l);
+  for (int k = 0; k < NE; ++k)
+    for (int l = k + 1; l < NE; ++l) {
+      double s = 0.5 * (Be[(size_t)k * NE + l] + Be[(size_t)l * NE + k]);
+      Be[(size_t)k * NE + l] = Be[(size_t)l * NE + k] = s;
+    }
+  for (int k = 0; k < NO; ++k)
+    for (int l = k + 1; l < NO; ++l) {
+      double s = 0.5 * (Bo[(size_t)k * NO + l] + Bo[(size_t)l * NO + k]);
+      Bo[(size_t)k * NO + l] = Bo[(size_t)l * NO + k] = s;
+    }
+  std::vector<double> Ve, le, Vo, lo;
+  jacobi_or_throw(NE, Be, Ve, le);
+  if (NO > 0) jacobi_or_throw(NO, Bo, Vo, lo);
+  // nodal values of the modes: node a < H of a symmetric mode = Ve[a][i] / (sqrt2 Msq[a]),
+  // middle node = Ve[H][i] / Msq[H]; antisymmetric: Vo[a][i] / (sqrt2 Msq[a]) (negated at n-1-a)
+  double* Se = S;
+  double* So = S + (size_t)NE * NE;
+  double* We = W;
+  double* Wo = W + (size_t)NE * NE;
+  for (int p = 0; p < NE; ++p)
+    for (int i = 0; i < NE; ++i) {
+      double s = Ve[(size_t)p * NE + i] * ((p < H) ? r2 : 1.0) / Msq[p];
+      Se[(size_t)p * NE + i] = s;
+      We[(size_t)i * NE + p] = w[p] * s;                         // transposed
+
+    }
+  for (int p = 0; p < NO; ++p)
+    for (int i = 0; i < NO; ++i) {
+      double s = Vo[(size_t)p * NO + i] * r2 / Msq[p];
+      So[(size_t)p * NO + i] = s;
+      Wo[(size_t)i * NO + p] = w[p] * s;                         // transposed
+    }
+  for (int i = 0; i < NE; ++i) lam[i] = le[i];
+  for (int i = 0; i < NO; ++i) lam[NE + i] = lo[i];
+  *sym = 1;
 }
 
 static int wrap_index(const Axis1DHost& a, int I) {
@@ -342,32 +436,38 @@ static int wrap_index(const Axis1DHost& a, int I) {
   return (I < 0 || I >= N) ? -1 : I;
 }
 
+static void alloc_tables(AxisTables& t) {
+  t.S.assign((size_t)t.count * t.n * t.n, 0.0);
+  t.W.assign((size_t)t.count * t.n * t.n, 0.0);
+  t.lam.assign((size_t)t.count * t.n, 0.0);
+  t.sym.assign(t.count, 0);
+}
+
 // Element-centred patches along one axis (Sec. 3.1): element m plus N_o node
 // layers of each neighbour: global 1-D range [m NP - N_o, m NP + NP + N_o).
 // Weights w_H (Eq. weight function:ec) with readings C6 and C18.
-void ec_axis_tables(const Axis1DHost& a, int No, int weighting, int& n, int& count, int& start0,
-                    std::vector<double>& S, std::vector<double>& lam, std::vector<double>& w) {
+void ec_axis_tables(const Axis1DHost& a, int No, int weighting, AxisTables& t) {
   const int NP = a.NP, Ne = a.Ne, P = a.P;
-  n = NP + 2 * No;
-  count = Ne;
-  start0 = -No;
-  S.assign((size_t)count * n * n, 0.0);
-  lam.assign((size_t)count * n, 0.0);
-  w.assign((size_t)count * n, 0.0);
+  t.n = NP + 2 * No;
+  t.count = Ne;
+  t.start0 = -No;
+  alloc_tables(t);
+  const int n = t.n;
   const double dxi = a.eta[No] + 1.0;
   for (int m = 0; m < Ne; ++m) {
     std::vector<int> g(n);
-    for (int t = 0; t < n; ++t) g[t] = wrap_index(a, m * NP - No + t);
+    std::vector<double> w(n, 0.0);
+    for (int s = 0; s < n; ++s) g[s] = wrap_index(a, m * NP - No + s);
     bool has_left = a.periodic || m > 0, has_right = a.periodic || m < Ne - 1;
-    for (int t = 0; t < n; ++t) {
-      if (g[t] < 0) continue;
+    for (int s = 0; s < n; ++s) {
+      if (g[s] < 0) continue;
       double xi;
-      if (t < No) {
-        xi = a.eta[P - No + 1 + t] - 2.0;
-      } else if (t < No + NP) {
-        xi = a.eta[t - No];
+      if (s < No) {
+        xi = a.eta[P - No + 1 + s] - 2.0;
+      } else if (s < No + NP) {
+        xi = a.eta[s - No];
       } else {
-        xi = a.eta[t - No - NP] + 2.0;
+        xi = a.eta[s - No - NP] + 2.0;
       }
       double wt = 1.0;
       if (No > 0) {
@@ -375,45 +475,111 @@ void ec_axis_tables(const Axis1DHost& a, int No, int weighting, int& n, int& cou
         double r = has_right ? transition((1.0 - xi) / dxi, weighting) : 1.0;
         wt = 0.5 * (l + r);
       }
-      w[(size_t)m * n + t] = wt;
+      w[s] = wt;
     }
-    patch_eig(a, g, &S[(size_t)m * n * n], &lam[(size_t)m * n]);
+    patch_tables(a, g, w, &t.S[(size_t)m * n * n], &t.W[(size_t)m * n * n], &t.lam[(size_t)m * n],
+                 &t.sym[m]);
   }
 }
 
 // Face-centred patches, normal axis (Sec. 3.1): face f between elements f-1
 // and f, global 1-D range [f NP - P, f NP + P) (far-face layers excluded).
 // Normal weight w_F = 1/2 [1 + phi(1 - |xi_F|)] (reading C5); walls: C13.
-void fc_axis_tables(const Axis1DHost& a, int weighting, int& n, int& count, int& start0,
-                    std::vector<double>& S, std::vector<double>& lam, std::vector<double>& w) {
+void fc_axis_tables(const Axis1DHost& a, int weighting, AxisTables& t) {
   const int NP = a.NP, Ne = a.Ne, P = a.P;
-  n = 2 * P;
-  count = a.periodic ? Ne : Ne + 1;
-  start0 = -P;
-  S.assign((size_t)count * n * n, 0.0);
-  lam.assign((size_t)count * n, 0.0);
-  w.assign((size_t)count * n, 0.0);
-  for (int f = 0; f < count; ++f) {
+  t.n = 2 * P;
+  t.count = a.periodic ? Ne : Ne + 1;
+  t.start0 = -P;
+  alloc_tables(t);
+  const int n = t.n;
+  for (int f = 0; f < t.count; ++f) {
     std::vector<int> g(n);
-    for (int t = 0; t < n; ++t) g[t] = wrap_index(a, f * NP - P + t);
-    for (int t = 0; t < n; ++t) {
-      if (g[t] < 0) continue;
-      // t < P: node t+1 of element f-1 (xi_F = eta - 1); else node t-P of element f (xi_F = eta + 1)
-      double xiF = (t < P) ? a.eta[t + 1] - 1.0 : a.eta[t - P] + 1.0;
-      w[(size_t)f * n + t] = 0.5 * (1.0 + transition(1.0 - std::fabs(xiF), weighting));
+    std::vector<double> w(n, 0.0);
+    for (int s = 0; s < n; ++s) g[s] = wrap_index(a, f * NP - P + s);
+    for (int s = 0; s < n; ++s) {
+      if (g[s] < 0) continue;
+      // s < P: node s+1 of element f-1 (xi_F = eta - 1); else node s-P of element f (xi_F = eta + 1)
+      double xiF = (s < P) ? a.eta[s + 1] - 1.0 : a.eta[s - P] + 1.0;
+      w[s] = 0.5 * (1.0 + transition(1.0 - std::fabs(xiF), weighting));
     }
-    patch_eig(a, g, &S[(size_t)f * n * n], &lam[(size_t)f * n]);
+    patch_tables(a, g, w, &t.S[(size_t)f * n * n], &t.W[(size_t)f * n * n], &t.lam[(size_t)f * n],
+                 &t.sym[f]);
   }
 }
 
-// Generalised eigen-pairs of the whole global 1-D operator (coarse solve).
+// Generalised eigen-pairs of the whole global 1-D operator (coarse solve),
+// general (unfolded) form.
 void global_axis_eig(const Axis1DHost& a, std::vector<double>& S, std::vector<double>& lam) {
-  int N = a.Ne * a.NP;
+  const int N = a.Ne * a.NP;
   std::vector<int> g(N);
   for (int i = 0; i < N; ++i) g[i] = i;
+  std::vector<double> B, Msq, V, l;
+  patch_matrix(a, g, B, Msq);
+  jacobi_or_throw(N, B, V, l);
   S.assign((size_t)N * N, 0.0);
-  lam.assign(N, 0.0);
-  patch_eig(a, g, S.data(), lam.data());
+  for (int p = 0; p < N; ++p)
+    for (int i = 0; i < N; ++i) S[(size_t)p * N + i] = V[(size_t)p * N + i] / Msq[p];
+  lam = l;
+}
+
+// Apply-kernel tables of one axis: per element m, Lt = M_m^-1 L^0_m (rows
+// scaled by the inverse diagonal mass, so the kernel scales by the nodal mass
+// product once per node), its centro-symmetry flag and, when symmetric, the
+// even-odd folded form: E[i][a] = (Lt[i][a] + Lt[i][P-a]) / 2 for a < H and
+// E[i][H] = Lt[i][H] (middle column, odd NP), rows i < NE; then
+// O[i][a] = (Lt[i][a] - Lt[i][P-a]) / 2, i, a < H.  Coupling row (2 NP + 8):
+// [-aL D0_i / M_i]_i, [aR DP_i / M_i]_i, bL/M_0, cL/M_0, hasL, bR/M_P, cR/M_P, hasR.
+void apply_axis_tables(const Axis1DHost& a, ApplyAxisHost& t) {
+  const int NP = a.NP, Ne = a.Ne, P = a.P;
+  const int H = NP / 2, NE = NP - H, NO = H;
+  t.L0.assign((size_t)Ne * NP * NP, 0.0);
+  t.cpl.assign((size_t)Ne * (2 * NP + 8), 0.0);
+  t.sym.assign(Ne, 0);
+  std::vector<double> Lt((size_t)NP * NP);
+  for (int m = 0; m < Ne; ++m) {
+    const double* M = &a.M[(size_t)m * NP];
+    const double* L0 = &a.L0[(size_t)m * NP * NP];
+    double big = 0.0;
+    for (int i = 0; i < NP; ++i)
+      for (int k = 0; k < NP; ++k) {
+        Lt[(size_t)i * NP + k] = L0[(size_t)i * NP + k] / M[i];
+        big = std::max(big, std::fabs(Lt[(size_t)i * NP + k]));
+      }
+    bool sym = NP >= 2;
+    for (int i = 0; i < NP && sym; ++i)
+      for (int k = 0; k < NP; ++k)
+        if (std::fabs(Lt[(size_t)i * NP + k] - Lt[(size_t)(P - i) * NP + (P - k)]) > 1e-13 * big) {
+          sym = false;
+          break;
+        }
+    double* dst = &t.L0[(size_t)m * NP * NP];
+    if (sym) {
+      double* E = dst;
+      double* O = dst + (size_t)NE * NE;
+      for (int i = 0; i < NE; ++i)
+        for (int c = 0; c < NE; ++c)
+          E[(size_t)i * NE + c] = (c < H) ? 0.5 * (Lt[(size_t)i * NP + c] + Lt[(size_t)i * NP + (P - c)])
+                                          : Lt[(size_t)i * NP + H];
+      for (int i = 0; i < NO; ++i)
+        for (int c = 0; c < NO; ++c)
+          O[(size_t)i * NO + c] = 0.5 * (Lt[(size_t)i * NP + c] - Lt[(size_t)i * NP + (P - c)]);
+    } else {
+      std::copy(Lt.begin(), Lt.end(), dst);
+    }
+    t.sym[m] = sym ? 1 : 0;
+    const double* c = &a.cpl[(size_t)m * 8];
+    double* o = &t.cpl[(size_t)m * (2 * NP + 8)];
+    for (int i = 0; i < NP; ++i) {
+      o[i] = c[3] != 0.0 ? -c[0] * a.D[0 * NP + i] / M[i] : 0.0;
+      o[NP + i] = c[7] != 0.0 ? c[4] * a.D[(size_t)P * NP + i] / M[i] : 0.0;
+    }
+    o[2 * NP + 0] = c[1] / M[0];
+    o[2 * NP + 1] = c[2] / M[0];
+    o[2 * NP + 2] = c[3];
+    o[2 * NP + 3] = c[5] / M[P];
+    o[2 * NP + 4] = c[6] / M[P];
+    o[2 * NP + 5] = c[7];
+  }
 }
 
 }  // namespace pmg

@@ -16,24 +16,20 @@ namespace pmg {
 
 std::atomic<unsigned long long> g_launches{0};
 
-int fdm_dispatch_d3(const LevelDims&, const FdmFamily<double>&, const double*, double*, double,
-                    cudaStream_t);
-int fdm_dispatch_d2(const LevelDims&, const FdmFamily<double>&, const double*, double*, double,
-                    cudaStream_t);
-int fdm_dispatch_f3(const LevelDims&, const FdmFamily<float>&, const float*, float*, float,
-                    cudaStream_t);
-int fdm_dispatch_f2(const LevelDims&, const FdmFamily<float>&, const float*, float*, float,
-                    cudaStream_t);
+int fdm_dispatch_d3(const LevelDims&, const FdmFamily<double>&, const double*, double*, cudaStream_t);
+int fdm_dispatch_d2(const LevelDims&, const FdmFamily<double>&, const double*, double*, cudaStream_t);
+int fdm_dispatch_f3(const LevelDims&, const FdmFamily<float>&, const float*, float*, cudaStream_t);
+int fdm_dispatch_f2(const LevelDims&, const FdmFamily<float>&, const float*, float*, cudaStream_t);
 
 template <>
 int launch_fdm<double>(const LevelDims& dm, const FdmFamily<double>& fam, const double* r,
-                       double* u, double omega, cudaStream_t s) {
-  return dm.dim == 3 ? fdm_dispatch_d3(dm, fam, r, u, omega, s) : fdm_dispatch_d2(dm, fam, r, u, omega, s);
+                       double* u, cudaStream_t s) {
+  return dm.dim == 3 ? fdm_dispatch_d3(dm, fam, r, u, s) : fdm_dispatch_d2(dm, fam, r, u, s);
 }
 template <>
 int launch_fdm<float>(const LevelDims& dm, const FdmFamily<float>& fam, const float* r, float* u,
-                      float omega, cudaStream_t s) {
-  return dm.dim == 3 ? fdm_dispatch_f3(dm, fam, r, u, omega, s) : fdm_dispatch_f2(dm, fam, r, u, omega, s);
+                      cudaStream_t s) {
+  return dm.dim == 3 ? fdm_dispatch_f3(dm, fam, r, u, s) : fdm_dispatch_f2(dm, fam, r, u, s);
 }
 
 namespace {
@@ -74,6 +70,12 @@ T* dev_upload(std::vector<void*>& owned, const std::vector<double>& host) {
   return d;
 }
 
+int* dev_upload_int(std::vector<void*>& owned, const std::vector<int>& host) {
+  int* d = dev_alloc<int>(owned, host.size() ? host.size() : 1);
+  if (!host.empty()) PMG_CUDA(cudaMemcpy(d, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return d;
+}
+
 // trivial third axis of a 2-D patch family
 template <typename T>
 FdmAxis<T> trivial_axis(std::vector<void*>& owned) {
@@ -85,18 +87,16 @@ FdmAxis<T> trivial_axis(std::vector<void*>& owned) {
   ax.periodic = 0;
   ax.phys = 2;
   ax.S = dev_upload<T>(owned, {1.0});
+  ax.W = dev_upload<T>(owned, {1.0});
   ax.lam = dev_upload<T>(owned, {0.0});
-  ax.w = dev_upload<T>(owned, {1.0});
+  ax.sym = dev_upload_int(owned, {0});
   return ax;
 }
 
-struct AxisTables {
-  int n, count, start0;
-  std::vector<double> S, lam, w;
-};
-
+// scale: omega for the first patch-buffer axis (folds the damping into W), 1 otherwise
 template <typename T>
-FdmAxis<T> upload_axis(std::vector<void*>& owned, const AxisTables& t, const Axis1DHost& a, int phys) {
+FdmAxis<T> upload_axis(std::vector<void*>& owned, const AxisTables& t, const Axis1DHost& a, int phys,
+                       double scale) {
   FdmAxis<T> ax{};
   ax.n = t.n;
   ax.count = t.count;
@@ -105,8 +105,11 @@ FdmAxis<T> upload_axis(std::vector<void*>& owned, const AxisTables& t, const Axi
   ax.periodic = a.periodic ? 1 : 0;
   ax.phys = phys;
   ax.S = dev_upload<T>(owned, t.S);
+  std::vector<double> W(t.W);
+  for (double& x : W) x *= scale;
+  ax.W = dev_upload<T>(owned, W);
   ax.lam = dev_upload<T>(owned, t.lam);
-  ax.w = dev_upload<T>(owned, t.w);
+  ax.sym = dev_upload_int(owned, t.sym);
   return ax;
 }
 
@@ -118,9 +121,12 @@ void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTab
   auto& own = dev.owned;
   for (int d = 0; d < 3; ++d) {
     int dd = d < dm.dim ? d : 0;
-    dev.at.L0[d] = dev_upload<T>(own, ax[dd].L0);
+    ApplyAxisHost t;
+    apply_axis_tables(ax[dd], t);
+    dev.at.L0[d] = dev_upload<T>(own, t.L0);
+    dev.at.sym[d] = dev_upload_int(own, t.sym);
     dev.at.M[d] = dev_upload<T>(own, ax[dd].M);
-    dev.at.cpl[d] = dev_upload<T>(own, ax[dd].cpl);
+    dev.at.cpl[d] = dev_upload<T>(own, t.cpl);
   }
   std::vector<double> D0(dm.NP), DP(dm.NP);
   for (int k = 0; k < dm.NP; ++k) {
@@ -138,7 +144,7 @@ void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTab
     fam.count_total = 1;
     for (int q = 0; q < 3; ++q) {
       if (q < dm.dim) {
-        fam.ax[q] = upload_axis<T>(own, ec[q], ax[q], q);
+        fam.ax[q] = upload_axis<T>(own, ec[q], ax[q], q, q == 0 ? h.opt.omega : 1.0);
         fam.count_total *= ec[q].count;
       } else {
         fam.ax[q] = trivial_axis<T>(own);
@@ -148,12 +154,12 @@ void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTab
   } else {
     for (int nrm = 0; nrm < dm.dim; ++nrm) {
       FdmFamily<T> fam{};
-      fam.ax[0] = upload_axis<T>(own, fc[nrm], ax[nrm], nrm);
+      fam.ax[0] = upload_axis<T>(own, fc[nrm], ax[nrm], nrm, h.opt.omega);
       fam.count_total = fc[nrm].count;
       int q = 1;
       for (int d = 0; d < dm.dim; ++d) {
         if (d == nrm) continue;
-        fam.ax[q] = upload_axis<T>(own, ec[d], ax[d], d);
+        fam.ax[q] = upload_axis<T>(own, ec[d], ax[d], d, 1.0);
         fam.count_total *= ec[d].count;
         ++q;
       }
@@ -186,7 +192,6 @@ template <typename T>
 void smooth_level(Hier& h, int l, T* u, const T* f, int nsteps, bool u_zero, cudaStream_t s) {
   LevelDev<T>& d = lev<T>(h, l);
   const LevelDims& dm = h.dims[l];
-  const T omega = (T)h.opt.omega;
   for (int st = 0; st < nsteps; ++st) {
     if (h.opt.smoother == PMG_SMOOTHER_EA) {
       const T* r = f;
@@ -194,7 +199,7 @@ void smooth_level(Hier& h, int l, T* u, const T* f, int nsteps, bool u_zero, cud
         PMG_CHECK(launch_apply<T>(dm, d.at, u, f, d.r, s));
         r = d.r;
       }
-      PMG_CHECK(launch_fdm<T>(dm, d.ea, r, u, omega, s));
+      PMG_CHECK(launch_fdm<T>(dm, d.ea, r, u, s));
     } else {
       for (int nrm = 0; nrm < dm.dim; ++nrm) {       // reading C12: same order pre and post
         const T* r = f;
@@ -202,7 +207,7 @@ void smooth_level(Hier& h, int l, T* u, const T* f, int nsteps, bool u_zero, cud
           PMG_CHECK(launch_apply<T>(dm, d.at, u, f, d.r, s));
           r = d.r;
         }
-        PMG_CHECK(launch_fdm<T>(dm, d.fa[nrm], r, u, omega, s));
+        PMG_CHECK(launch_fdm<T>(dm, d.fa[nrm], r, u, s));
       }
     }
   }
@@ -262,6 +267,43 @@ void precondition(Hier& h, const double* r, double* z, cudaStream_t s) {
   }
 }
 
+// z = V-cycle(r) on the MGCG work vectors, replayed from a CUDA graph after the
+// first direct call (the direct call also performs one-time kernel set-up).
+void precondition_graph(Hier& h, cudaStream_t s) {
+  if (h.pc_state == 1) {
+    PMG_CUDA(cudaGraphLaunch(h.pc_exec, s));
+    g_launches.fetch_add(h.pc_launches, std::memory_order_relaxed);
+    return;
+  }
+  if (h.pc_state == 0 && h.pc_calls++ >= 1) {
+    if (!h.cap_stream) PMG_CUDA(cudaStreamCreateWithFlags(&h.cap_stream, cudaStreamNonBlocking));
+    const unsigned long long c0 = g_launches.load();
+    bool ok = cudaStreamBeginCapture(h.cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      try {
+        precondition(h, h.r, h.z, h.cap_stream);
+      } catch (const CudaError&) {
+        ok = false;
+      }
+      cudaGraph_t graph = nullptr;
+      ok = (cudaStreamEndCapture(h.cap_stream, &graph) == cudaSuccess) && ok && graph;
+      if (ok) ok = cudaGraphInstantiate(&h.pc_exec, graph, 0) == cudaSuccess;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();                     // clear a failed capture
+    g_launches.store(c0);                   // captured launches did not run
+    if (ok) {
+      h.pc_state = 1;                        // pc_launches: kernels per V-cycle, from the direct call
+      precondition_graph(h, s);
+      return;
+    }
+    h.pc_state = -1;
+  }
+  const unsigned long long c0 = g_launches.load();
+  precondition(h, h.r, h.z, s);
+  if (h.pc_state == 0) h.pc_launches = g_launches.load() - c0;
+}
+
 void read_scalars(Hier& h, cudaStream_t s, int* status) {
   PMG_CUDA(cudaMemcpyAsync(h.hscal, h.scal, sizeof(double) * S_NUM, cudaMemcpyDeviceToHost, s));
   PMG_CUDA(cudaMemcpyAsync(h.hscal + S_NUM, h.dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -290,7 +332,8 @@ int solve_impl(Hier& h, const double* g, double* u, double rtol, pmg_stats* st, 
   }
   if (!(r0 == r0)) return PMG_ENAN;
   if (r0 == 0.0) return PMG_OK;
-  precondition(h, h.r, h.p, s);
+  precondition_graph(h, s);
+  PMG_CUDA(cudaMemcpyAsync(h.p, h.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   launch_dot(h.p, h.r, nullptr, n, h.partial, h.counter, h.scal + S_DELTA, nb, s);
   int rc = PMG_ENOCONV;
   for (int it = 1; it <= h.opt.max_iter; ++it) {
@@ -307,7 +350,7 @@ int solve_impl(Hier& h, const double* g, double* u, double rtol, pmg_stats* st, 
     }
     if (status != 0) { rc = status; break; }
     if (rn <= rtol * r0) { rc = PMG_OK; break; }
-    precondition(h, h.r, h.z, s);
+    precondition_graph(h, s);
     launch_dot(h.z, h.r, it >= 2 ? h.r_old : nullptr, n, h.partial, h.counter, h.scal + S_ZR, nb, s);
     launch_p_update(h.p, h.z, h.scal, it == 1 ? 1 : 0, n, s);
     launch_set_delta(h.scal, h.dstatus, s);
@@ -343,6 +386,8 @@ void free_all(Hier* h) {
   }
   for (void* p : h->owned) cudaFree(p);
   if (h->hscal) cudaFreeHost(h->hscal);
+  if (h->pc_exec) cudaGraphExecDestroy(h->pc_exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
 }
 
 }  // namespace
@@ -458,16 +503,18 @@ int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
       std::vector<AxisTables> ec(dim), fc(dim);
       if (l > 0) {
         for (int d = 0; d < dim; ++d) {
-          AxisTables& t = ec[d];
-          ec_axis_tables(h->axes[l][d], h->No[l], o.weighting, t.n, t.count, t.start0, t.S, t.lam, t.w);
+          ec_axis_tables(h->axes[l][d], h->No[l], o.weighting, ec[d]);
           if (o.smoother == PMG_SMOOTHER_FA) {
-            AxisTables& u = fc[d];
-            fc_axis_tables(h->axes[l][d], o.weighting, u.n, u.count, u.start0, u.S, u.lam, u.w);
+            fc_axis_tables(h->axes[l][d], o.weighting, fc[d]);
           }
         }
       }
       build_level_dev<double>(*h, l, h->d64[l], ec, fc);
       if (o.precision == PMG_PREC_MIXED) build_level_dev<float>(*h, l, h->d32[l], ec, fc);
+      for (auto& t : ec) { t.S.clear(); t.W.clear(); t.lam.clear(); }
+      for (auto& t : fc) { t.S.clear(); t.W.clear(); t.lam.clear(); }
+      h->ec_shape[l] = ec;
+      h->fc_shape[l] = fc;
       if (l > 0) {
         std::vector<double> J;
         lagrange_matrix(h->axes[l - 1][0].eta, h->axes[l][0].eta, J);
@@ -661,6 +708,45 @@ const char* pmg_last_error(pmg_hier hh) { return hh ? H(hh)->err.c_str() : ""; }
 
 unsigned long long pmg_kernel_launches(void) { return g_launches.load(); }
 
+int pmg_schwarz_sweep_fma(pmg_hier hh, int level, int family, double* fma) {
+  Hier* h = H(hh);
+  if (!h || !fma || level < 1 || level > h->L) return PMG_EINVAL;
+  const LevelDims& dm = h->dims[level];
+  const bool ea = h->opt.smoother == PMG_SMOOTHER_EA;
+  if (ea ? family != -1 : (family < 0 || family >= dm.dim)) return PMG_EINVAL;
+  // patch-buffer axes of the family, in kernel order
+  const AxisTables* ax[3] = {nullptr, nullptr, nullptr};
+  if (ea) {
+    for (int q = 0; q < dm.dim; ++q) ax[q] = &h->ec_shape[level][q];
+  } else {
+    ax[0] = &h->fc_shape[level][family];
+    int q = 1;
+    for (int d = 0; d < dm.dim; ++d)
+      if (d != family) ax[q++] = &h->ec_shape[level][d];
+  }
+  const int nd = dm.dim;
+  // per axis: sum over positions of the multiply-adds of one line pass (even-odd: NE^2 + NO^2)
+  double per_axis[3] = {0, 0, 0}, count[3] = {1, 1, 1}, n[3] = {1, 1, 1};
+  for (int q = 0; q < nd; ++q) {
+    const int nn = ax[q]->n, H = nn / 2, NE = nn - H;
+    n[q] = nn;
+    count[q] = ax[q]->count;
+    for (int p = 0; p < ax[q]->count; ++p) per_axis[q] += ax[q]->sym[p] ? double(NE * NE + H * H) : double(nn * nn);
+  }
+  double total = 0.0;
+  for (int q = 0; q < nd; ++q) {
+    double lines = 1.0, others = 1.0;     // lines of a patch along q, and patch count of the other axes
+    for (int r = 0; r < nd; ++r)
+      if (r != q) {
+        lines *= n[r];
+        others *= count[r];
+      }
+    total += 2.0 * lines * others * per_axis[q];        // forward + backward pass
+  }
+  *fma = total;
+  return PMG_OK;
+}
+
 int pmg_schwarz_sweep(pmg_hier hh, int level, int family, const double* r, double* u, void* stream) {
   Hier* h = H(hh);
   if (!h || level < 1 || level > h->L || !r || !u) return PMG_EINVAL;
@@ -673,11 +759,11 @@ int pmg_schwarz_sweep(pmg_hier hh, int level, int family, const double* r, doubl
       LevelDev<float>& d = h->d32[level];
       launch_convert<double, float>(r, d.r, dm.ndof, s);
       launch_convert<double, float>(u, d.u, dm.ndof, s);
-      PMG_CHECK(launch_fdm<float>(dm, ea ? d.ea : d.fa[family], d.r, d.u, (float)h->opt.omega, s));
+      PMG_CHECK(launch_fdm<float>(dm, ea ? d.ea : d.fa[family], d.r, d.u, s));
       launch_convert<float, double>(d.u, u, dm.ndof, s);
     } else {
       LevelDev<double>& d = h->d64[level];
-      PMG_CHECK(launch_fdm<double>(dm, ea ? d.ea : d.fa[family], r, u, h->opt.omega, s));
+      PMG_CHECK(launch_fdm<double>(dm, ea ? d.ea : d.fa[family], r, u, s));
     }
     PMG_CUDA(cudaGetLastError());
     return PMG_OK;

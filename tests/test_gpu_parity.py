@@ -27,6 +27,10 @@ CASES = [
     (3, 4, (3, 3, 2), [[0.3, 0.5, 0.2], [0.2, 0.3, 0.5], [0.6, 0.4]], True, 0.0),
     (3, 8, (2, 3, 2), [[0.5, 0.5], [0.3, 0.3, 0.4], [0.7, 0.3]], False, 0.0),
     (3, 16, (2, 1, 2), [[0.5, 0.5], [1.0], [0.5, 0.5]], False, 0.5),
+    # uniform grids: interior patches are centro-symmetric (even-odd split in the kernel)
+    (3, 8, (4, 3, 3), [[0.25] * 4, [1 / 3] * 3, [1 / 3] * 3], False, 0.0),
+    (3, 4, (3, 4, 3), [[1 / 3] * 3, [0.25] * 4, [1 / 3] * 3], True, 0.0),
+    (2, 8, (5, 4), [[0.2] * 5, [0.25] * 4], True, 0.0),
 ]
 IDS = [f"{c[0]}d-P{c[1]}-{'x'.join(map(str, c[2]))}-{'per' if c[4] else 'dir'}-b{c[5]}" for c in CASES]
 
