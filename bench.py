@@ -293,46 +293,53 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
     nelem = int(np.prod(w.n_elem))
     No = 1 + (w.P + 4) // 8
     nn = NP + 2 * No
-    # --- Schwarz patch kernel alone (EA, finest level): the dominant kernel of the solve
-    r = torch.empty_like(g)
-    h.residual(h.L, torch.zeros_like(g), g, r)
-    uu = torch.zeros_like(g)
+    # --- Schwarz patch kernel alone (finest level, the hierarchy's own arithmetic): the dominant kernel
     fam = -1 if opts["smoother"] == "EA" else 0
+    fp64_main = args.precision == "fp64"
+    tname = "double" if fp64_main else "float"
 
-    def sweep(hier=h, x=uu):
-        st = lib.pmg_schwarz_sweep(hier.handle, hier.L, fam, binding._ptr(r), binding._ptr(x),
-                                   binding._stream(stream))
+    def native(hier=h):
+        st = lib.pmg_schwarz_sweep_native(hier.handle, hier.L, fam, binding._stream(stream))
         assert st == 0, st
-    sweep()
-    ms = time_kernel(sweep, 10, stream, flush)
+    native()
+    ms = time_kernel(native, 10, stream, flush)
     # algorithmic flops of one launch as implemented: 2 x the multiply-adds of the six line
     # passes (even-odd split on centro-symmetric axes), reported by the library
     flops = 2.0 * h.schwarz_sweep_fma(h.L, fam)
-    paper_flops = 12.0 * nn ** 4 * nelem       # the paper's count: 6 passes of n^4 per n^3 patch
+    paper_flops = 12.0 * nn ** 4 * nelem if fam == -1 else None   # the paper's n^4-per-pass count (EA)
+    peak = (FP64_PEAK_GFLOPS if fp64_main else FP32_PEAK_GFLOPS) / 1e3
     ach = flops / (ms * 1e-3) / 1e12
-    line["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                        "frac": ach / (FP64_PEAK_GFLOPS / 1e3), "traffic": None,
-                        "kernel": (f"fdm_kernel<double,{nn},{nn},{nn}> (EA patch solve, P={w.P})"
+    # DRAM bytes per patch of this kernel from one ncu capture of the same kernel on the
+    # 32^3-element P = 8 problem (profiles/fdm_kernel_double_13_poisson3d_32cube_P8.md),
+    # scaled by patches; only for the kernel version that was captured
+    traffic = None
+    if fam == -1 and fp64_main and w.P == 8 and w.dim == 3:
+        traffic = (382.78e6 + 153.36e6) / 32768 * nelem
+    line["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                        "frac": ach / peak, "traffic": traffic,
+                        "kernel": (f"fdm_kernel<{tname},{nn},{nn},{nn}> (EA patch solve, P={w.P})"
                                    if fam == -1 else
-                                   f"fdm_kernel<double,{2 * w.P},{nn},{nn}> (FA patch solve, x faces, P={w.P})"),
+                                   f"fdm_kernel<{tname},{2 * w.P},{nn},{nn}> (FA patch solve, x faces, P={w.P})"),
                         "flops_per_launch": flops, "paper_count_flops_per_launch": paper_flops,
-                        "peak_source": "FP64 FMA throughput measured on this pool's GB300 (nominal "
-                                       "1.25 TFLOP/s); FP64 is ALU-bound here (~270 flop per 24 B/DOF)"}
+                        "peak_source": ("FP64" if fp64_main else "FP32") + " FMA throughput measured on this "
+                                       "pool's GB300 (FMA-chain probe; nominal FP64 1.25 TFLOP/s); the patch "
+                                       "solve does ~270 flop per 24 B/DOF, far above both ridges"}
     line["smoother"] = {"gdof_s": n / (ms * 1e-3) / 1e9, "ms_patch_sweep": ms,
                         "note": ("EA" if fam == -1 else "FA (one direction)")
-                                + " patch sweep alone (gather, 6 transforms, weighted scatter), FP64"}
-    # apply kernel (FP64): share of the solve
+                                + f" patch sweep alone (gather, 6 transforms, weighted scatter), {tname}"}
+    # apply kernel (FP64, the outer CG's operator): share of the solve
+    r = torch.empty_like(g)
     ms_apply = time_kernel(lambda: h.apply(h.L, g, r), 10, stream, flush)
-    line["apply"] = {"ms": ms_apply, "gdof_s": n / (ms_apply * 1e-3) / 1e9,
-                     "gflops": (6.0 * NP + 12) * n / (ms_apply * 1e-3) / 1e9}
-    # --- mixed-precision V-cycle (FP32 smoother/transfers/residuals inside FP64 CG)
-    hm = Hierarchy(grid, precision="mixed", **opts)
+    line["apply"] = {"ms": ms_apply, "gdof_s": n / (ms_apply * 1e-3) / 1e9, "dtype": "f64"}
+    # --- the other arithmetic on the same problem: mixed (fp32 V-cycle inside the FP64 CG) vs FP64
+    other = "mixed" if fp64_main else "fp64"
+    hm = Hierarchy(grid, precision=other, **opts)
     um = torch.zeros_like(g)
-    for _ in range(2):
+    for _ in range(1):
         um.zero_()
         hm.solve(g, um, rtol=1e-10, history=False)
     tm, itm = [], 0
-    for _ in range(max(2, args.steps)):
+    for _ in range(max(2, min(args.steps, 3))):
         flush.fill_(1.0)
         um.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -345,18 +352,16 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
     u.zero_()
     h.solve(g, u, rtol=1e-10, history=False)
     rel = float((um - u).abs().max() / u.abs().max())
-    um2 = torch.zeros_like(g)
-
-    def sweep_m():
-        st = lib.pmg_schwarz_sweep(hm.handle, hm.L, fam, binding._ptr(r), binding._ptr(um2),
-                                   binding._stream(stream))
-        assert st == 0
-    ms_m = time_kernel(sweep_m, 10, stream, flush)
-    line["mixed"] = {"value": n / (statistics.mean(tm) * 1e-3), "unit": "DOF/s",
-                     "ms_per_step": statistics.mean(tm), "iterations": itm, "status": rc,
-                     "max_rel_diff_vs_fp64_solution": rel,
-                     "speedup_vs_fp64": statistics.mean(tm) and line["ms_per_step"] / statistics.mean(tm),
-                     "patch_sweep_ms_incl_fp64_fp32_staging": ms_m}
+    ms_o = time_kernel(lambda: native(hm), 5, stream, flush)
+    t_o = statistics.mean(tm)
+    entry = {"value": n / (t_o * 1e-3), "unit": "DOF/s", "ms_per_step": t_o, "iterations": itm,
+             "status": rc, "max_rel_diff_between_solutions": rel, "patch_sweep_ms": ms_o}
+    if fp64_main:
+        entry["speedup_vs_fp64"] = line["ms_per_step"] / t_o
+        line["mixed"] = entry
+    else:
+        line["fp64_plain"] = entry
+        line["speedup_vs_fp64"] = t_o / line["ms_per_step"]
     hm.close()
     # --- end to end through the host-buffer C-ABI call (pinned host memory)
     g_host = g.cpu().pin_memory()

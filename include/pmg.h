@@ -71,6 +71,14 @@ typedef struct {
   double omega;        /* damping of the additive update                  (default 1) */
   int precision;       /* PMG_PREC_*                                      (default FP64) */
   int max_iter;        /* MGCG iteration cap (Algorithm 2, i_max)         (default 100) */
+  /* Per-level smoother parameters (index = level l = 1..L; entry 0 unused), e.g.
+   * from a learned model; 0 selects the default.  omega_level: damping of level l
+   * (default omega).  tau_level in (0, 1]: width of the weight transition zone
+   * relative to the paper's (w_H over tau * dxi_O; w_F = 1/2 [1 + phi((1-|xi_F|)/tau)]);
+   * default 1 = the paper's weights.  Any tau in (0, 1] keeps the weights a
+   * partition of unity. */
+  double omega_level[8];
+  double tau_level[8];
 } pmg_options;
 
 typedef struct {
@@ -208,9 +216,43 @@ int pmg_solve_host(pmg_hier h, const double* g_host, double* u_host, double rtol
 int pmg_schwarz_sweep(pmg_hier h, int level, int family, const double* r_dev, double* u_dev,
                       void* stream);
 
+/*
+ * Learned smoother parameters (spec extension; the paper fixes omega = 1
+ * and the weight transition): a small fp32 MLP mapping the features of one level
+ * (log2 P_l, N_o, three log2 element aspect ratios, l/L) to two raw outputs,
+ * which paper_1603_02524_gb300.learned maps to (omega_l, tau_l) for
+ * pmg_options.omega_level / tau_level.  Network 6 -> 64 tanh -> 64 tanh -> 2;
+ * parameters theta packed as W1[6][64], b1[64], W2[64][64], b2[64], W3[64][2], b3[2]
+ * (PMG_MLP_NPARAM floats).  All pointers are device pointers; row-major batches.
+ */
+#define PMG_MLP_IN 6
+#define PMG_MLP_HIDDEN 64
+#define PMG_MLP_OUT 2
+#define PMG_MLP_NPARAM 4738
+/* y[batch][2] = MLP(x[batch][6]); h1, h2 (batch x 64, may be NULL) keep the hidden
+ * activations for pmg_mlp_backward. */
+int pmg_mlp_forward(const float* theta, const float* x, int batch, float* y, float* h1, float* h2,
+                    void* stream);
+/* grad[PMG_MLP_NPARAM] = d loss / d theta and *loss (device scalar, may be NULL) for
+ * loss = (1/batch) sum_b weight_b sum_o (y_bo - target_bo)^2 (weight may be NULL = 1),
+ * from the activations of pmg_mlp_forward.  work: batch x PMG_MLP_NPARAM floats of
+ * scratch (per-sample gradients, summed in a fixed order: deterministic). */
+int pmg_mlp_backward(const float* theta, const float* x, const float* h1, const float* h2,
+                     const float* y, const float* target, const float* weight, int batch, float* grad,
+                     float* loss, float* work, void* stream);
+/* One Adam step (bias-corrected, step >= 1) on n parameters with moments m, v. */
+int pmg_mlp_adam(float* theta, const float* grad, float* m, float* v, int n, int step, float lr,
+                 float beta1, float beta2, float eps, void* stream);
+
 /* Text for a status code; last error detail of a hierarchy (may be ""). */
 const char* pmg_status_string(int status);
 const char* pmg_last_error(pmg_hier h);
+
+/* Benchmark hook: one sweep of (level, family) in the hierarchy's own
+ * arithmetic (fp32 in mixed precision) on its internal level buffers, whose
+ * contents are arbitrary; no staging copies, nothing the caller owns is read
+ * or written.  For timing the patch kernel alone. */
+int pmg_schwarz_sweep_native(pmg_hier h, int level, int family, void* stream);
 
 /* Multiply-adds one pmg_schwarz_sweep of (level, family) executes in its six
  * eigenvector line passes, as implemented (even-odd split on centro-symmetric

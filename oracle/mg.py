@@ -48,7 +48,9 @@ class Hierarchy:
 
     def __init__(self, dim, P, spacing, periodic, beta=0.0, mu_star=1.0, smoother="EA",
                  overlap="l", weighting="quintic", ns=(1, 1), variable=False, omega=1.0,
-                 coarse="cg", coarse_rtol=1e-14):
+                 coarse="cg", coarse_rtol=1e-14, omega_level=None, tau_level=None):
+        """omega_level / tau_level: optional per-level damping and transition width
+        (index = level l; entries for l >= 1), overriding omega and tau = 1."""
         L = int(round(math.log2(P)))
         if 2 ** L != P:
             raise ValueError("P must be a power of two (P_l = 2^l)")
@@ -62,7 +64,9 @@ class Hierarchy:
             sm = None
             nsl = (0, 0)
             if l > 0:
-                sm = Smoother(disc, smoother, overlap, weighting, omega)
+                om = omega_level[l] if omega_level is not None else omega
+                ta = tau_level[l] if tau_level is not None else 1.0
+                sm = Smoother(disc, smoother, overlap, weighting, om, tau=ta)
                 fac = 2 ** (L - l) if variable else 1
                 nsl = (ns[0] * fac, ns[1] * fac)
             self.levels.append(Level(disc, sm, nsl))

@@ -98,8 +98,13 @@ class AxisPatch:
         self.lam, self.S = sla.eigh(Ls, Ms)
 
 
-def ec_axis(axis, m, No, weighting):
-    """Element-centred patch of element m along one axis (Sec. 3.1)."""
+def ec_axis(axis, m, No, weighting, tau=1.0):
+    """Element-centred patch of element m along one axis (Sec. 3.1).
+
+    tau in (0, 1] narrows the transition zone of w_H to tau * dxi_O (an extension for
+    learned smoother parameters; tau = 1 is the paper's weight).  For tau <= 1 the
+    weights stay a partition of unity: phi is odd and the zone stays inside the overlap.
+    """
     P, NP, Ne, eta = axis.P, axis.NP, axis.Ne, axis.eta
     idx, xi = [], []
     has_left = axis.periodic or m > 0
@@ -121,15 +126,19 @@ def ec_axis(axis, m, No, weighting):
     if No == 0:
         w = np.ones_like(xi)                                            # C6
     else:
-        dxi = eta[No] + 1.0
+        dxi = (eta[No] + 1.0) * tau
         left = phi((1 + xi) / dxi, weighting) if has_left else 1.0       # C18
         right = phi((1 - xi) / dxi, weighting) if has_right else 1.0     # C18
         w = 0.5 * (left + right) * np.ones_like(xi)     # both terms may be the wall limit 1
     return AxisPatch(idx, w, axis)
 
 
-def fc_axis(axis, f, weighting):
-    """Face-centred patch, normal direction, face f between elements f-1 and f (Sec. 3.1, C5, C13)."""
+def fc_axis(axis, f, weighting, tau=1.0):
+    """Face-centred patch, normal direction, face f between elements f-1 and f (Sec. 3.1, C5, C13).
+
+    tau in (0, 1] narrows the transition of w_F around the element centres:
+    w_F = 1/2 [1 + phi((1 - |xi_F|) / tau)] (tau = 1: reading C5).
+    """
     P, NP, Ne, eta = axis.P, axis.NP, axis.Ne, axis.eta
     idx, xiF = [], []
     if axis.periodic or f > 0:
@@ -143,7 +152,7 @@ def fc_axis(axis, f, weighting):
             idx.append(mr * NP + i)
             xiF.append(eta[i] + 1.0)
     xiF = np.asarray(xiF)
-    w = 0.5 * (1.0 + phi(1.0 - np.abs(xiF), weighting))                 # C5
+    w = 0.5 * (1.0 + phi((1.0 - np.abs(xiF)) / tau, weighting))         # C5
     return AxisPatch(idx, w, axis)
 
 
@@ -210,7 +219,7 @@ class Smoother:
     """
 
     def __init__(self, disc: Discretisation, kind="EA", overlap="l", weighting="quintic", omega=1.0,
-                 symmetrize=None):
+                 symmetrize=None, tau=1.0):
         self.disc = disc
         self.kind = kind
         # reading C11: FM symmetrised, EM not
@@ -218,11 +227,12 @@ class Smoother:
         self.No = overlap_nodes(disc.P, overlap)
         self.weighting = weighting
         self.omega = omega
+        self.tau = tau
         dim = disc.dim
-        self.ec = [[ec_axis(disc.axes[d], m, self.No, weighting) for m in range(disc.axes[d].Ne)]
+        self.ec = [[ec_axis(disc.axes[d], m, self.No, weighting, tau) for m in range(disc.axes[d].Ne)]
                    for d in range(dim)]
         if kind in ("FA", "FM"):
-            self.fc = [[fc_axis(disc.axes[d], f, weighting) for f in range(n_faces(disc.axes[d]))]
+            self.fc = [[fc_axis(disc.axes[d], f, weighting, tau) for f in range(n_faces(disc.axes[d]))]
                        for d in range(dim)]
 
     # -- subdomain enumeration (lexicographic: x fastest) ----------------

@@ -26,13 +26,15 @@ EXPORTS = ["pmg_options_default", "pmg_grid_create", "pmg_grid_destroy", "pmg_gr
            "pmg_apply", "pmg_residual", "pmg_rhs", "pmg_smooth", "pmg_restrict", "pmg_prolong",
            "pmg_coarse_solve", "pmg_vcycle", "pmg_solve", "pmg_solve_host", "pmg_status_string",
            "pmg_last_error", "pmg_schwarz_sweep", "pmg_kernel_launches", "pmg_coarse_solve_static",
-           "pmg_schwarz_sweep_fma"]
+           "pmg_schwarz_sweep_fma", "pmg_schwarz_sweep_native", "pmg_mlp_forward",
+           "pmg_mlp_backward", "pmg_mlp_adam"]
 
 
 class PmgOptions(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("overlap", ctypes.c_int), ("weighting", ctypes.c_int),
                 ("ns_pre", ctypes.c_int), ("ns_post", ctypes.c_int), ("variable_v", ctypes.c_int),
-                ("omega", ctypes.c_double), ("precision", ctypes.c_int), ("max_iter", ctypes.c_int)]
+                ("omega", ctypes.c_double), ("precision", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("omega_level", ctypes.c_double * 8), ("tau_level", ctypes.c_double * 8)]
 
 
 class PmgStats(ctypes.Structure):
@@ -86,6 +88,11 @@ def load(path: str | None = None):
         "pmg_kernel_launches": (ctypes.c_ulonglong, []),
         "pmg_coarse_solve_static": (i, [vp, vp, vp, vp]),
         "pmg_schwarz_sweep_fma": (i, [vp, i, i, ctypes.POINTER(ctypes.c_double)]),
+        "pmg_schwarz_sweep_native": (i, [vp, i, i, vp]),
+        "pmg_mlp_forward": (i, [vp, vp, i, vp, vp, vp, vp]),
+        "pmg_mlp_backward": (i, [vp, vp, vp, vp, vp, vp, vp, i, vp, vp, vp, vp]),
+        "pmg_mlp_adam": (i, [vp, vp, vp, vp, i, i, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             ctypes.c_float, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -96,7 +103,8 @@ def load(path: str | None = None):
 
 
 def options(smoother="EA", overlap="l", weighting="quintic", ns=(1, 1), variable_v=False,
-            omega=1.0, precision="fp64", max_iter=100) -> PmgOptions:
+            omega=1.0, precision="fp64", max_iter=100, omega_level=None, tau_level=None) -> PmgOptions:
+    """omega_level / tau_level: optional per-level sequences (index = level, 0 = default)."""
     o = PmgOptions()
     load().pmg_options_default(ctypes.byref(o))
     o.smoother = SMOOTHER[smoother]
@@ -107,6 +115,10 @@ def options(smoother="EA", overlap="l", weighting="quintic", ns=(1, 1), variable
     o.omega = float(omega)
     o.precision = PRECISION[precision]
     o.max_iter = int(max_iter)
+    for l, v in enumerate(omega_level or []):
+        o.omega_level[l] = float(v)
+    for l, v in enumerate(tau_level or []):
+        o.tau_level[l] = float(v)
     return o
 
 

@@ -173,8 +173,18 @@ __device__ __forceinline__ double recip(double s) {
 }
 __device__ __forceinline__ float recip(float s) { return __frcp_rn(s); }
 
+// CTA size: enough threads for the widest line pass (one line per thread),
+// rounded to whole warps, at most 256.
+template <int NA, int NB, int NC>
+constexpr int fdm_threads() {
+  constexpr int l0 = NB * NC, l1 = NA * NC, l2 = NA * NB;
+  constexpr int m = l0 > l1 ? (l0 > l2 ? l0 : l2) : (l1 > l2 ? l1 : l2);
+  constexpr int t = (m + 31) / 32 * 32;
+  return t < 256 ? t : 256;
+}
+
 template <typename T, int NA, int NB, int NC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(fdm_threads<NA, NB, NC>())
 fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restrict__ u) {
   constexpr int NN = NA * NB * NC;
   extern __shared__ __align__(16) unsigned char fdm_smem[];
@@ -298,7 +308,7 @@ int fdm_launch(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, c
   attr_done = true;
   if (fam.count_total <= 0) return PMG_OK;
   count_launch();
-  fdm_kernel<T, NA, NB, NC><<<fam.count_total, 256, smem, s>>>(dm, fam, r, u);
+  fdm_kernel<T, NA, NB, NC><<<fam.count_total, fdm_threads<NA, NB, NC>(), smem, s>>>(dm, fam, r, u);
   return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
 }
 

@@ -181,8 +181,8 @@ void lagrange_matrix(const std::vector<double>& nodes, const std::vector<double>
 int sym_eig_jacobi(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& lam);
 int overlap_nodes(int P_l, int policy);
 double transition(double x, int weighting);
-void ec_axis_tables(const Axis1DHost& a, int No, int weighting, AxisTables& t);
-void fc_axis_tables(const Axis1DHost& a, int weighting, AxisTables& t);
+void ec_axis_tables(const Axis1DHost& a, int No, int weighting, double tau, AxisTables& t);
+void fc_axis_tables(const Axis1DHost& a, int weighting, double tau, AxisTables& t);
 void global_axis_eig(const Axis1DHost& a, std::vector<double>& S, std::vector<double>& lam);
 
 // ----------------------------------------------------------------------------

@@ -446,14 +446,14 @@ static void alloc_tables(AxisTables& t) {
 // Element-centred patches along one axis (Sec. 3.1): element m plus N_o node
 // layers of each neighbour: global 1-D range [m NP - N_o, m NP + NP + N_o).
 // Weights w_H (Eq. weight function:ec) with readings C6 and C18.
-void ec_axis_tables(const Axis1DHost& a, int No, int weighting, AxisTables& t) {
+void ec_axis_tables(const Axis1DHost& a, int No, int weighting, double tau, AxisTables& t) {
   const int NP = a.NP, Ne = a.Ne, P = a.P;
   t.n = NP + 2 * No;
   t.count = Ne;
   t.start0 = -No;
   alloc_tables(t);
   const int n = t.n;
-  const double dxi = a.eta[No] + 1.0;
+  const double dxi = (a.eta[No] + 1.0) * tau;      // tau < 1: narrower transition (learned knob)
   for (int m = 0; m < Ne; ++m) {
     std::vector<int> g(n);
     std::vector<double> w(n, 0.0);
@@ -485,7 +485,7 @@ void ec_axis_tables(const Axis1DHost& a, int No, int weighting, AxisTables& t) {
 // Face-centred patches, normal axis (Sec. 3.1): face f between elements f-1
 // and f, global 1-D range [f NP - P, f NP + P) (far-face layers excluded).
 // Normal weight w_F = 1/2 [1 + phi(1 - |xi_F|)] (reading C5); walls: C13.
-void fc_axis_tables(const Axis1DHost& a, int weighting, AxisTables& t) {
+void fc_axis_tables(const Axis1DHost& a, int weighting, double tau, AxisTables& t) {
   const int NP = a.NP, Ne = a.Ne, P = a.P;
   t.n = 2 * P;
   t.count = a.periodic ? Ne : Ne + 1;
@@ -500,7 +500,7 @@ void fc_axis_tables(const Axis1DHost& a, int weighting, AxisTables& t) {
       if (g[s] < 0) continue;
       // s < P: node s+1 of element f-1 (xi_F = eta - 1); else node s-P of element f (xi_F = eta + 1)
       double xiF = (s < P) ? a.eta[s + 1] - 1.0 : a.eta[s - P] + 1.0;
-      w[s] = 0.5 * (1.0 + transition(1.0 - std::fabs(xiF), weighting));
+      w[s] = 0.5 * (1.0 + transition((1.0 - std::fabs(xiF)) / tau, weighting));
     }
     patch_tables(a, g, w, &t.S[(size_t)f * n * n], &t.W[(size_t)f * n * n], &t.lam[(size_t)f * n],
                  &t.sym[f]);

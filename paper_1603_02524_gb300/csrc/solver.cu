@@ -76,6 +76,14 @@ int* dev_upload_int(std::vector<void*>& owned, const std::vector<int>& host) {
   return d;
 }
 
+// per-level smoother parameters (0 selects the default)
+double level_omega(const pmg_options& o, int l) {
+  return (l >= 1 && l < 8 && o.omega_level[l] > 0.0) ? o.omega_level[l] : o.omega;
+}
+double level_tau(const pmg_options& o, int l) {
+  return (l >= 1 && l < 8 && o.tau_level[l] > 0.0) ? o.tau_level[l] : 1.0;
+}
+
 // trivial third axis of a 2-D patch family
 template <typename T>
 FdmAxis<T> trivial_axis(std::vector<void*>& owned) {
@@ -144,7 +152,7 @@ void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTab
     fam.count_total = 1;
     for (int q = 0; q < 3; ++q) {
       if (q < dm.dim) {
-        fam.ax[q] = upload_axis<T>(own, ec[q], ax[q], q, q == 0 ? h.opt.omega : 1.0);
+        fam.ax[q] = upload_axis<T>(own, ec[q], ax[q], q, q == 0 ? level_omega(h.opt, l) : 1.0);
         fam.count_total *= ec[q].count;
       } else {
         fam.ax[q] = trivial_axis<T>(own);
@@ -154,7 +162,7 @@ void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTab
   } else {
     for (int nrm = 0; nrm < dm.dim; ++nrm) {
       FdmFamily<T> fam{};
-      fam.ax[0] = upload_axis<T>(own, fc[nrm], ax[nrm], nrm, h.opt.omega);
+      fam.ax[0] = upload_axis<T>(own, fc[nrm], ax[nrm], nrm, level_omega(h.opt, l));
       fam.count_total = fc[nrm].count;
       int q = 1;
       for (int d = 0; d < dm.dim; ++d) {
@@ -408,6 +416,7 @@ void pmg_options_default(pmg_options* opt) {
   opt->omega = 1.0;
   opt->precision = PMG_PREC_FP64;
   opt->max_iter = 100;
+  for (int l = 0; l < 8; ++l) opt->omega_level[l] = opt->tau_level[l] = 0.0;
 }
 
 int pmg_grid_create(int dim, int P, const int n_elem[3], const double* const spacing[3],
@@ -465,6 +474,8 @@ int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
   if (o.overlap < 0 || o.overlap > 2) return PMG_EINVAL;
   if (o.weighting != 0 && o.weighting != 1 && o.weighting != 3 && o.weighting != 5) return PMG_EINVAL;
   if (o.ns_pre < 0 || o.ns_post < 0 || o.max_iter < 1 || !(o.omega > 0.0)) return PMG_EINVAL;
+  for (int l = 0; l < 8; ++l)
+    if (!(o.omega_level[l] >= 0.0) || !(o.tau_level[l] >= 0.0) || o.tau_level[l] > 1.0) return PMG_EINVAL;
   if (o.precision != PMG_PREC_FP64 && o.precision != PMG_PREC_MIXED) return PMG_EINVAL;
   Hier* h = nullptr;
   try {
@@ -503,9 +514,9 @@ int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
       std::vector<AxisTables> ec(dim), fc(dim);
       if (l > 0) {
         for (int d = 0; d < dim; ++d) {
-          ec_axis_tables(h->axes[l][d], h->No[l], o.weighting, ec[d]);
+          ec_axis_tables(h->axes[l][d], h->No[l], o.weighting, level_tau(o, l), ec[d]);
           if (o.smoother == PMG_SMOOTHER_FA) {
-            fc_axis_tables(h->axes[l][d], o.weighting, fc[d]);
+            fc_axis_tables(h->axes[l][d], o.weighting, level_tau(o, l), fc[d]);
           }
         }
       }
@@ -707,6 +718,26 @@ const char* pmg_status_string(int status) {
 const char* pmg_last_error(pmg_hier hh) { return hh ? H(hh)->err.c_str() : ""; }
 
 unsigned long long pmg_kernel_launches(void) { return g_launches.load(); }
+
+int pmg_schwarz_sweep_native(pmg_hier hh, int level, int family, void* stream) {
+  Hier* h = H(hh);
+  if (!h || level < 1 || level > h->L) return PMG_EINVAL;
+  const LevelDims& dm = h->dims[level];
+  const bool ea = h->opt.smoother == PMG_SMOOTHER_EA;
+  if (ea ? family != -1 : (family < 0 || family >= dm.dim)) return PMG_EINVAL;
+  return guarded(h, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->opt.precision == PMG_PREC_MIXED) {
+      LevelDev<float>& d = h->d32[level];
+      PMG_CHECK(launch_fdm<float>(dm, ea ? d.ea : d.fa[family], d.f, d.u, s));
+    } else {
+      LevelDev<double>& d = h->d64[level];
+      PMG_CHECK(launch_fdm<double>(dm, ea ? d.ea : d.fa[family], d.f, d.u, s));
+    }
+    PMG_CUDA(cudaGetLastError());
+    return PMG_OK;
+  });
+}
 
 int pmg_schwarz_sweep_fma(pmg_hier hh, int level, int family, double* fma) {
   Hier* h = H(hh);

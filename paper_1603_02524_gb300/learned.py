@@ -1,0 +1,210 @@
+"""Learned Schwarz smoother parameters (spec extension; the paper fixes them).
+
+A small MLP (6 -> 64 -> 64 -> 2, fp32, trained and evaluated by the library's own
+CUDA kernels pmg_mlp_forward / pmg_mlp_backward / pmg_mlp_adam) maps the features
+of one p-level of a hierarchy
+
+    x = [log2 P_l, N_o,l, a_1, a_2, a_3, l / L],
+    a_1 >= a_2 >= a_3 = 0: log2 of each axis' median element width over the smallest,
+
+to two raw outputs, turned into the level's smoother parameters
+
+    omega_l = 0.5 + sigmoid(y_0)          damping of the additive update, in (0.5, 1.5)
+    tau_l   = 0.1 + 0.9 sigmoid(y_1)      width of the weight transition, in (0.1, 1)
+
+(pmg_options.omega_level / tau_level).  The paper's method is omega = tau = 1.
+Training targets come from the method's own runs: for each generated grid the MGCG
+residual-reduction rate rho = (r_n / r_0)^(1/n) is measured for a set of candidate
+(omega, tau) pairs, and the best pair becomes the target of every level of that
+grid; samples are weighted by the rate gain over the paper's parameters.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import binding
+from .binding import Grid, Hierarchy
+
+NPARAM = 4738
+IN, HID, OUT = 6, 64, 2
+
+
+def overlap_nodes(P_l: int, policy: str = "l") -> int:
+    """N_o of level l, as the library's default policy (1 + round(P_l / 8))."""
+    if policy == "0":
+        return 0
+    if policy == "lf":
+        return 1 + P_l // 8
+    return 1 + (P_l + 4) // 8
+
+
+def aspect_features(spacing) -> list:
+    med = [float(np.median(s)) for s in spacing] + [None] * (3 - len(spacing))
+    hs = [m for m in med if m is not None]
+    hmin = min(hs)
+    a = sorted((math.log2(m / hmin) for m in hs), reverse=True)
+    return (a + [0.0, 0.0, 0.0])[:3]
+
+
+def level_features(P: int, spacing, overlap: str = "l") -> np.ndarray:
+    """Feature rows for levels 1..L of a hierarchy of order P (row l-1 = level l)."""
+    L = int(round(math.log2(P)))
+    a = aspect_features(spacing)
+    rows = []
+    for l in range(1, L + 1):
+        Pl = 2 ** l
+        rows.append([math.log2(Pl), overlap_nodes(Pl, overlap), a[0], a[1], a[2], l / L])
+    return np.asarray(rows, dtype=np.float32)
+
+
+def to_params(y: np.ndarray):
+    omega = 0.5 + 1.0 / (1.0 + np.exp(-y[:, 0]))
+    tau = 0.1 + 0.9 / (1.0 + np.exp(-y[:, 1]))
+    return omega, tau
+
+
+def to_raw(omega, tau) -> np.ndarray:
+    o = np.clip(np.asarray(omega, dtype=np.float64) - 0.5, 1e-3, 1 - 1e-3)
+    t = np.clip((np.asarray(tau, dtype=np.float64) - 0.1) / 0.9, 1e-3, 1 - 1e-3)
+    return np.stack([np.log(o / (1 - o)), np.log(t / (1 - t))], axis=-1).astype(np.float32)
+
+
+def init_theta(seed: int = 0) -> np.ndarray:
+    """Glorot-uniform weights, zero biases (float32, packed as in include/pmg.h)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for fan_in, fan_out in ((IN, HID), (HID, HID), (HID, OUT)):
+        lim = math.sqrt(6.0 / (fan_in + fan_out))
+        parts += [g.uniform(-lim, lim, size=fan_in * fan_out), np.zeros(fan_out)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+class SmootherMLP:
+    """The network on the device; forward, training and prediction through the C ABI."""
+
+    def __init__(self, theta: np.ndarray | None = None, device="cuda"):
+        import torch
+        self.torch = torch
+        self.device = device
+        th = init_theta() if theta is None else np.asarray(theta, dtype=np.float32)
+        assert th.size == NPARAM
+        self.theta = torch.from_numpy(th.copy()).to(device)
+        self.m = torch.zeros_like(self.theta)
+        self.v = torch.zeros_like(self.theta)
+        self.step = 0
+
+    def _ptr(self, t):
+        return binding._ptr(t)
+
+    def forward(self, x: np.ndarray, keep=False):
+        torch = self.torch
+        xt = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(self.device)
+        B = xt.shape[0]
+        y = torch.empty(B, OUT, dtype=torch.float32, device=self.device)
+        h1 = torch.empty(B, HID, dtype=torch.float32, device=self.device)
+        h2 = torch.empty_like(h1)
+        st = binding.load().pmg_mlp_forward(self._ptr(self.theta), self._ptr(xt), B, self._ptr(y),
+                                            self._ptr(h1), self._ptr(h2), binding._stream())
+        if st != 0:
+            raise binding.PmgError("pmg_mlp_forward", st)
+        return (y, h1, h2, xt) if keep else y.cpu().numpy()
+
+    def loss_and_grad(self, x, t, w=None):
+        torch = self.torch
+        y, h1, h2, xt = self.forward(x, keep=True)
+        B = xt.shape[0]
+        tt = torch.from_numpy(np.ascontiguousarray(t, dtype=np.float32)).to(self.device)
+        wt = None if w is None else torch.from_numpy(np.ascontiguousarray(w, dtype=np.float32)).to(self.device)
+        grad = torch.empty_like(self.theta)
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        work = torch.empty(B * NPARAM, dtype=torch.float32, device=self.device)
+        st = binding.load().pmg_mlp_backward(self._ptr(self.theta), self._ptr(xt), self._ptr(h1), self._ptr(h2),
+                                             self._ptr(y), self._ptr(tt), self._ptr(wt) if wt is not None else None,
+                                             B, self._ptr(grad), self._ptr(loss), self._ptr(work),
+                                             binding._stream())
+        if st != 0:
+            raise binding.PmgError("pmg_mlp_backward", st)
+        return loss, grad
+
+    def adam_step(self, grad, lr=3e-3, b1=0.9, b2=0.999, eps=1e-8):
+        self.step += 1
+        st = binding.load().pmg_mlp_adam(self._ptr(self.theta), self._ptr(grad), self._ptr(self.m),
+                                         self._ptr(self.v), NPARAM, self.step, lr, b1, b2, eps,
+                                         binding._stream())
+        if st != 0:
+            raise binding.PmgError("pmg_mlp_adam", st)
+
+    def train(self, x, t, w=None, steps=2000, lr=3e-3):
+        history = []
+        for k in range(steps):
+            loss, grad = self.loss_and_grad(x, t, w)
+            self.adam_step(grad, lr=lr)
+            if k % 100 == 0 or k == steps - 1:
+                history.append(float(loss.item()))
+        return history
+
+    def level_params(self, P, spacing, overlap="l"):
+        """omega_level, tau_level lists (index = level) for a hierarchy of order P."""
+        y = self.forward(level_features(P, spacing, overlap))
+        om, ta = to_params(y)
+        return [0.0] + [float(v) for v in om], [0.0] + [float(v) for v in ta]
+
+
+# ---------------------------------------------------------------------------
+# measurements with the library
+# ---------------------------------------------------------------------------
+
+@dataclass
+class GridConfig:
+    P: int
+    n_elem: tuple
+    aspect: tuple                    # element width ratios hx : hy : hz
+    smoother: str = "EA"
+    periodic: bool = False
+
+    def spacing(self):
+        return [[a / n] * n for a, n in zip(self.aspect, self.n_elem)]
+
+
+def measure_rate(cfg: GridConfig, omega_level=None, tau_level=None, iters=8, seed=0):
+    """MGCG residual-reduction rate rho = (r_n / r_0)^(1/n) on a seeded random RHS."""
+    import torch
+    g = Grid(3, cfg.P, cfg.n_elem, cfg.spacing(), periodic=cfg.periodic)
+    h = Hierarchy(g, smoother=cfg.smoother, overlap="l", max_iter=iters, omega_level=omega_level,
+                  tau_level=tau_level)
+    n = h.ndof()
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    f = torch.rand(n, dtype=torch.float64, device="cuda", generator=gen) * 2 - 1
+    u = torch.zeros_like(f)
+    rc, it, hist = h.solve(f, u, rtol=1e-13)
+    h.close()
+    g.close()
+    hist = [x for x in hist if x > 0]
+    k = len(hist) - 1
+    return (hist[-1] / hist[0]) ** (1.0 / k) if k > 0 else 0.0
+
+
+CANDIDATES = [(om, ta) for om in (0.8, 0.9, 1.0, 1.1, 1.2) for ta in (0.3, 0.6, 1.0)]
+
+
+def make_dataset(configs, candidates=CANDIDATES, iters=8):
+    """Features, raw targets and weights from the best measured candidate per grid."""
+    X, T, W, records = [], [], [], []
+    for cfg in configs:
+        L = int(round(math.log2(cfg.P)))
+        rates = {}
+        for om, ta in candidates:
+            rates[(om, ta)] = measure_rate(cfg, [0.0] + [om] * L, [0.0] + [ta] * L, iters=iters)
+        base = measure_rate(cfg, None, None, iters=iters)
+        best = min(rates, key=rates.get)
+        gain = math.log(max(base, 1e-300) / max(rates[best], 1e-300))
+        feats = level_features(cfg.P, cfg.spacing())
+        for row in feats:
+            X.append(row)
+            T.append(to_raw(best[0], best[1]))
+            W.append(0.2 + gain)
+        records.append({"config": cfg, "rates": rates, "paper_rate": base, "best": best})
+    return np.asarray(X, np.float32), np.asarray(T, np.float32), np.asarray(W, np.float32), records

@@ -233,3 +233,31 @@ def test_invalid_arguments():
     lib = binding.load()
     assert lib.pmg_apply(h.handle, 99, None, None, None) == -1
     assert lib.pmg_smooth(h.handle, 0, None, None, 1, None) == -1
+
+
+@pytest.mark.parametrize("kind", ["EA", "FA"])
+def test_per_level_parameters(kind):
+    """Per-level damping omega_l and transition width tau_l (learned-parameter knobs):
+    smoothing steps and a full V-cycle against the oracle with the same parameters."""
+    case = CASES[7]                       # uniform 3-D, P = 8: even-odd path with narrowed weights
+    dim, P, ne, sp, per, beta = case
+    omega_level = [0.0, 0.85, 1.1, 0.9]
+    tau_level = [0.0, 0.5, 0.75, 0.3]
+    g, h = make(case, smoother=kind, omega_level=omega_level, tau_level=tau_level)
+    for l in range(1, h.L + 1):
+        shape = elem_shape(dim, ne, 2 ** l)
+        u, f = rnd(shape, 30 + l), rnd(shape, 40 + l)
+        disc = dg.Discretisation(dim, 2 ** l, sp, per, beta, 1.0)
+        sm = schwarz.Smoother(disc, kind, "l", "quintic", omega=omega_level[l], tau=tau_level[l])
+        ref = g2e(sm.step(e2g(u, dim), e2g(f, dim)), ne, 2 ** l)
+        ut = to_dev(u)
+        h.smooth(l, ut, to_dev(f), 1)
+        assert rel_err(from_dev(ut, shape), ref) < 1e-11, l
+    oh = OHier(dim, P, sp, per, beta, smoother=kind, coarse="dense", omega_level=omega_level,
+               tau_level=tau_level)
+    shape = elem_shape(dim, ne, P)
+    F = e2g(rnd(shape, 50), dim)
+    out = torch.zeros(int(np.prod(shape)), dtype=torch.float64, device="cuda")
+    h.vcycle(to_dev(g2e(F, ne, P)), out)
+    ref = g2e(oh.vcycle(np.zeros_like(F), F), ne, P)
+    assert rel_err(from_dev(out, shape), ref) < 1e-10

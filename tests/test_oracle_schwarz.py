@@ -44,6 +44,20 @@ def test_partition_of_unity(periodic, weighting, P, overlap):
             assert np.abs(_coverage(disc, sm, nrm) - 1).max() < 1e-14
 
 
+@pytest.mark.parametrize("tau", [0.25, 0.5, 0.9])
+def test_partition_of_unity_narrowed_transition(tau):
+    # the learned-parameter extension narrows the transition zone; weights must still sum to 1
+    disc = dg.Discretisation(2, 8, [[0.2, 0.3, 0.5], [0.25] * 4], False)
+    for kind in ("EA", "FA"):
+        sm = schwarz.Smoother(disc, kind, "l", "quintic", tau=tau)
+        for nrm in ([None] if kind == "EA" else [0, 1]):
+            assert np.abs(_coverage(disc, sm, nrm) - 1).max() < 1e-14
+    # tau = 1 reproduces the paper's weights exactly
+    a = schwarz.Smoother(disc, "EA", "l", "quintic")
+    b = schwarz.Smoother(disc, "EA", "l", "quintic", tau=1.0)
+    assert all(np.array_equal(x.w, y.w) for x, y in zip(a.ec[0], b.ec[0]))
+
+
 def test_partition_of_unity_single_element_axis():
     # one element between two walls: both transition terms take their wall limit (C18)
     disc = dg.Discretisation(3, 4, [[0.5, 0.5], [1.0], [0.3, 0.3, 0.4]], False)
