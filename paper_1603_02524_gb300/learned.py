@@ -9,14 +9,15 @@ of one p-level of a hierarchy
 
 to two raw outputs, turned into the level's smoother parameters
 
-    omega_l = 0.5 + sigmoid(y_0)          damping of the additive update, in (0.5, 1.5)
+    omega_l = 0.5 + 1.5 sigmoid(y_0)      damping of the additive update, in (0.5, 2)
     tau_l   = 0.1 + 0.9 sigmoid(y_1)      width of the weight transition, in (0.1, 1)
 
 (pmg_options.omega_level / tau_level).  The paper's method is omega = tau = 1.
 Training targets come from the method's own runs: for each generated grid the MGCG
 residual-reduction rate rho = (r_n / r_0)^(1/n) is measured for a set of candidate
-(omega, tau) pairs, and the best pair becomes the target of every level of that
-grid; samples are weighted by the rate gain over the paper's parameters.
+(omega, tau) pairs, and the best pair (robust to a +-0.05 error in omega, see
+robust_best) becomes the target of every level of that grid; samples are
+weighted by the rate gain over the paper's parameters.
 """
 from __future__ import annotations
 
@@ -61,13 +62,13 @@ def level_features(P: int, spacing, overlap: str = "l") -> np.ndarray:
 
 
 def to_params(y: np.ndarray):
-    omega = 0.5 + 1.0 / (1.0 + np.exp(-y[:, 0]))
+    omega = 0.5 + 1.5 / (1.0 + np.exp(-y[:, 0]))
     tau = 0.1 + 0.9 / (1.0 + np.exp(-y[:, 1]))
     return omega, tau
 
 
 def to_raw(omega, tau) -> np.ndarray:
-    o = np.clip(np.asarray(omega, dtype=np.float64) - 0.5, 1e-3, 1 - 1e-3)
+    o = np.clip((np.asarray(omega, dtype=np.float64) - 0.5) / 1.5, 1e-3, 1 - 1e-3)
     t = np.clip((np.asarray(tau, dtype=np.float64) - 0.1) / 0.9, 1e-3, 1 - 1e-3)
     return np.stack([np.log(o / (1 - o)), np.log(t / (1 - t))], axis=-1).astype(np.float32)
 
@@ -162,7 +163,7 @@ class GridConfig:
     P: int
     n_elem: tuple
     aspect: tuple                    # element width ratios hx : hy : hz
-    smoother: str = "EA"
+    smoother: str = "FA"
     periodic: bool = False
 
     def spacing(self):
@@ -189,7 +190,36 @@ def measure_rate(cfg: GridConfig, omega_level=None, tau_level=None, iters=8, see
     return (hist[-1] / hist[0]) ** (1.0 / k) if k > 0 else 0.0
 
 
-CANDIDATES = [(om, ta) for om in (0.8, 0.9, 1.0, 1.1, 1.2) for ta in (0.3, 0.6, 1.0)]
+# Candidate (omega, tau) pairs.  Measured on 4^3-element grids, P = 2..8: the paper's
+# EA smoother is already optimal at omega = tau = 1 (gains below 1 %), while the FA
+# smoother gains up to 2.6x in rate from over-relaxation (best omega 1.1..1.3;
+# omega >= 1.4 often breaks the flexible CG down), so the default set targets FA.
+OMEGAS = (1.0, 1.05, 1.1, 1.15, 1.2, 1.25, 1.3, 1.35, 1.4)
+TAUS = (0.5, 1.0)
+CANDIDATES = [(om, ta) for om in OMEGAS for ta in TAUS]
+
+
+def robust_best(rates):
+    """Candidate minimising the worst rate over itself and its omega neighbours (+-0.05):
+    the rate rises steeply past the optimum (a cliff between omega 1.2 and 1.3 on
+    stretched grids), so the target keeps a margin against the network's error."""
+    def score(key):
+        om, ta = key
+        near = [rates[(o, ta)] for o in OMEGAS if abs(o - om) <= 0.051 and (o, ta) in rates]
+        return (max(near), rates[key])
+    return min(rates, key=score)
+
+TRAIN_ASPECTS = [(1, 1, 1), (2, 1, 1), (8, 1, 1), (32, 1, 1), (8, 8, 1), (32, 32, 1), (16, 4, 1), (4, 2, 1)]
+HELDOUT_ASPECTS = [(4, 1, 1), (16, 1, 1), (4, 4, 1), (32, 8, 1), (16, 16, 1), (8, 2, 1)]
+
+
+def train_default(P_values=(2, 4, 8), steps=1500, seed=0, iters=8):
+    """Generate the training grids (FA, 4^3 elements), measure, train a fresh network."""
+    configs = [GridConfig(P, (4, 4, 4), a) for P in P_values for a in TRAIN_ASPECTS]
+    X, T, W, records = make_dataset(configs, iters=iters)
+    net = SmootherMLP(init_theta(seed))
+    hist = net.train(X, T, W, steps=steps)
+    return net, hist, records
 
 
 def make_dataset(configs, candidates=CANDIDATES, iters=8):
@@ -201,7 +231,7 @@ def make_dataset(configs, candidates=CANDIDATES, iters=8):
         for om, ta in candidates:
             rates[(om, ta)] = measure_rate(cfg, [0.0] + [om] * L, [0.0] + [ta] * L, iters=iters)
         base = measure_rate(cfg, None, None, iters=iters)
-        best = min(rates, key=rates.get)
+        best = robust_best(rates)
         gain = math.log(max(base, 1e-300) / max(rates[best], 1e-300))
         feats = level_features(cfg.P, cfg.spacing())
         for row in feats:

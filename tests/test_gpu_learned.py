@@ -49,3 +49,33 @@ def test_mlp_training_reduces_loss():
     net = SmootherMLP()
     hist = net.train(x, t, steps=600, lr=3e-3)
     assert hist[-1] < 0.05 * hist[0]
+
+
+def test_learned_parameters_beat_paper_parameters_on_heldout_grids(capsys):
+    """Train the MLP on rates measured by the library's own MGCG runs (FA smoother, 4^3
+    elements, P = 2, 4, 8, training aspect ratios), then compare, on held-out aspect
+    ratios, the measured rate with the network's per-level (omega, tau) against the
+    paper's omega = tau = 1."""
+    import math
+
+    from paper_1603_02524_gb300 import learned
+    net, hist, records = learned.train_default()
+    assert hist[-1] < 0.5 * hist[0]
+    gains, rows = [], []
+    for P in (2, 4, 8):
+        for a in learned.HELDOUT_ASPECTS:
+            cfg = learned.GridConfig(P, (4, 4, 4), a)
+            om, ta = net.level_params(P, cfg.spacing())
+            paper = learned.measure_rate(cfg)
+            mlp = learned.measure_rate(cfg, om, ta)
+            gains.append(math.log(paper / mlp))
+            rows.append((P, a, paper, mlp, om[1:], ta[1:]))
+            # never clearly worse than the paper's parameters on a held-out grid
+            assert mlp <= 1.10 * paper, rows[-1]
+    mean_gain = sum(gains) / len(gains)
+    with capsys.disabled():
+        for P, a, paper, mlp, om, ta in rows:
+            print(f"  P={P} aspect={a}: rate paper {paper:.4f} learned {mlp:.4f} "
+                  f"(omega {', '.join(f'{x:.2f}' for x in om)}; tau {', '.join(f'{x:.2f}' for x in ta)})")
+        print(f"  mean rate reduction on held-out grids: x{math.exp(mean_gain):.2f}")
+    assert mean_gain > math.log(1.15)      # the learned parameters converge measurably faster
