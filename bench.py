@@ -47,12 +47,30 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2ldg", "c2x32", "c3", "c4"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2ldg", "c2x32", "c3", "c4", "c5"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
-                    help="arithmetic of the timed solve's V-cycle (the outer CG is always FP64)")
-    return ap.parse_args()
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed_tc"],
+                    help="arithmetic of the timed solve's V-cycle (the outer CG is always FP64); "
+                         "default fp64, mixed for the batched workload c5")
+    ap.add_argument("--autotune", action="store_true",
+                    help="autotune the patch kernel's CTA size before timing (always on for c5)")
+    ap.add_argument("--outer-apply", default="fp64", choices=["fp64", "df"],
+                    help="arithmetic of the CG's own operator apply: FP64, or double-float on the FP32 pipes")
+    args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "mixed" if args.workload == "c5" else "fp64"
+    return args
+
+
+# arithmetic label per (V-cycle precision, outer apply)
+DTYPE = {("fp64", "fp64"): "f64", ("mixed", "fp64"): "f64+f32", ("mixed_tc", "fp64"): "f64+f32(tf32x3)",
+         ("fp64", "df"): "f64+df32", ("mixed", "df"): "f64+df32+f32", ("mixed_tc", "df"): "f64+df32+f32(tf32x3)"}
+# the solve's variants compared in the extras: label -> (V-cycle precision, outer apply)
+VARIANTS = {"fp64_plain": ("fp64", "fp64"), "mixed": ("mixed", "fp64"), "mixed_tc": ("mixed_tc", "fp64"),
+            "mixed_df": ("mixed", "df")}
+BATCH_OPTS = dict(smoother="FA", overlap="l", variable_v=True)
+BATCH_NAME = "batched_64grids_4rhs_3d_P4-16_aspect1-16"
 
 
 def workload(name):
@@ -150,7 +168,8 @@ def oracle_baseline(w, opts, budget_s=30.0):
     # about 1.2 M unknowns: 12^3 elements at P = 8, 6^3 at P = 16
     side = max(2, round((1.2e6 / (w.P + 1) ** w.dim) ** (1.0 / w.dim)))
     ne = tuple(min(n, side) for n in w.n_elem)
-    sp = [syn.uniform_spacing(n, 1.0) if len(set(s)) == 1 else list(s[:n]) for n, s in zip(ne, w.spacing)]
+    sp = [list(s) if n == len(s) else (syn.uniform_spacing(n, float(sum(s))) if len(set(s)) == 1 else list(s[:n]))
+          for n, s in zip(ne, w.spacing)]
     sw = syn.Workload(w.name + "_sample", w.dim, w.P, ne, sp, w.periodic, w.beta, w.mu_star, w.rhs, w.seed)
     t0 = time.perf_counter()
     h = OHier(w.dim, w.P, sp, w.periodic, w.beta, w.mu_star, smoother=opts["smoother"],
@@ -170,11 +189,18 @@ def oracle_baseline(w, opts, budget_s=30.0):
             "iterations": len(hist) - 1, "seconds": t2 - t1}
 
 
+def batch_oracle_sample():
+    """The smallest member of the batched workload (8^3 elements, P = 4), one right-hand side."""
+    members = syn.config5()
+    w = min(members, key=lambda m: m.ndof)
+    return w, dict(BATCH_OPTS)
+
+
 def run_reference(args):
     rank, world = dist_init(args)
     if rank != 0:
         return
-    w, opts = workload(args.workload)
+    w, opts = batch_oracle_sample() if args.workload == "c5" else workload(args.workload)
     vals = []
     base = None
     for k in range(args.warmup + args.steps):
@@ -191,17 +217,169 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DOF/s", "n_gpus": 0,
             "steps": len(vals), "warmup": args.warmup, "ms_per_step": 1e3 * w.ndof / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name, "sample": base["sample"]},
+            "data": "synthetic",
+            "config": {"workload": BATCH_NAME if args.workload == "c5" else w.name, "sample": base["sample"]},
             "cpu_baseline": {"value": v, "unit": "DOF/s", "cores": base["cores"], "kind": "oracle",
                              "sample": base["sample"]},
             "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+def main_batch(args):
+    """Workload c5: 64 independent 3-D grids (n^3 elements, n in {8,12,16,24}; P in {4,8,16};
+    element aspect ratios 1..16), 4 seeded Gaussian right-hand sides each, all solved to
+    1e-10 by one batched call (one CUDA graph launch); value = all solves' DOF / time."""
+    import torch
+    from paper_1603_02524_gb300 import Batch, Grid, Hierarchy, binding
+
+    rank, world = dist_init(args)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = binding.load()
+    members = syn.config5()
+    t0 = time.perf_counter()
+    grids, hiers, gs, us = [], [], [], []
+    for w in members:
+        grid = Grid(w.dim, w.P, w.n_elem, w.spacing, periodic=w.periodic, mu_star=w.mu_star, beta=w.beta)
+        grids.append(grid)
+        for k in range(w.extra["n_rhs"]):
+            h = Hierarchy(grid, precision=args.precision, **BATCH_OPTS)
+            f = syn.gauss_noise(w, seed=w.seed * 8 + k)
+            ft = torch.from_numpy(np.ascontiguousarray(f).reshape(-1)).to(dev)
+            g = torch.empty_like(ft)
+            h.rhs(ft, g)
+            hiers.append(h)
+            gs.append(g)
+            us.append(torch.zeros_like(g))
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for h in hiers:                      # tile (CTA) sizes per patch shape, cached per shape
+        h.autotune()
+    t_tune = time.perf_counter() - t0
+    ndof = [h.ndof() for h in hiers]
+    total = int(sum(ndof))
+    t0 = time.perf_counter()
+    b = Batch(hiers, gs, us, rtol=1e-10)
+    t_capture = time.perf_counter() - t0
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for u in us:
+            u.zero_()
+        return b.solve()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    launches0 = lib.pmg_kernel_launches()
+    times, res = [], None
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, res = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        assert rc == 0, f"batch status {rc}"
+    torch.cuda.synchronize()
+    launches = lib.pmg_kernel_launches() - launches0
+    clk = clocks.stop()
+    barrier(world)
+    t_step = max_over_ranks(statistics.mean(times), world, dev)
+    its = [r[1] for r in res]
+    line = {"metric": METRIC, "value": world * total / (t_step * 1e-3), "unit": "DOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+            "config": {"workload": BATCH_NAME, "solves": len(hiers),
+                       "grids": len(members), "total_dof": total, "max_dof": max(ndof), "min_dof": min(ndof),
+                       "smoother": "FA_l variable V", "precision": args.precision, "rtol": 1e-10,
+                       "iterations_min_median_max": [min(its), int(statistics.median(its)), max(its)],
+                       "l2": "flushed between steps (256 MB write); 4 GB of vectors", "one_graph_launch": True,
+                       "setup_s": t_setup, "autotune_s": t_tune, "capture_s": t_capture,
+                       "parallelism": f"replicas{world}"},
+            "gpu_launches": int(launches), "clocks": clk}
+    if not args.no_extras:
+        # the same solves one after another (each a captured single solve) on the same stream
+        for h, g, u in zip(hiers, gs, us):
+            u.zero_()
+            h.solve(g, u, rtol=1e-10, history=False)
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        for u in us:
+            u.zero_()
+        e0.record(stream)
+        for h, g, u in zip(hiers, gs, us):
+            h.solve(g, u, rtol=1e-10, history=False)
+        e1.record(stream)
+        e1.synchronize()
+        t_seq = e0.elapsed_time(e1)
+        line["sequential"] = {"ms": t_seq, "value": total / (t_seq * 1e-3), "unit": "DOF/s",
+                              "batch_speedup": t_seq / t_step,
+                              "note": "the same solves issued one after another (pmg_solve each)"}
+        # dominant kernel: the FA patch sweep on the finest level of the largest member
+        big = max(range(len(hiers)), key=lambda i: ndof[i])
+        hb = hiers[big]
+        wb = members[[i for i, w in enumerate(members) for _ in range(w.extra["n_rhs"])][big]]
+
+        def native():
+            st = lib.pmg_schwarz_sweep_native(hb.handle, hb.L, 0, binding._stream(stream))
+            assert st == 0, st
+        native()
+        ms = time_kernel(native, 10, stream, flush)
+        flops = 2.0 * hb.schwarz_sweep_fma(hb.L, 0)
+        fp64_main = args.precision == "fp64"
+        peak = (FP64_PEAK_GFLOPS if fp64_main else FP32_PEAK_GFLOPS) / 1e3
+        ach = flops / (ms * 1e-3) / 1e12
+        nn = wb.P + 1 + 2 * (1 + (wb.P + 4) // 8)
+        line["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                            "traffic": None,
+                            "kernel": f"fdm_kernel<{'double' if fp64_main else 'float'},{2 * wb.P},{nn},{nn}> "
+                                      f"(FA patch solve, x faces, largest member {wb.name})",
+                            "flops_per_launch": flops}
+        # end to end: pinned host right-hand sides in, solutions out, around the batched call
+        g_host = [g.cpu().pin_memory() for g in gs]
+        u_host = [torch.zeros(n, dtype=torch.float64).pin_memory() for n in ndof]
+        te = []
+        for _ in range(max(2, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for gd, gh in zip(gs, g_host):
+                gd.copy_(gh, non_blocking=True)
+            for u in us:
+                u.zero_()
+            b.solve()
+            for ud, uh in zip(us, u_host):
+                uh.copy_(ud, non_blocking=True)
+            torch.cuda.synchronize()
+            te.append(time.perf_counter() - t0)
+        line["e2e"] = {"value": total / statistics.mean(te), "unit": "DOF/s", "h2d_bytes_per_step": 8 * total,
+                       "d2h_bytes_per_step": 8 * total, "call": "pmg_batch_solve (g in; u out)"}
+        if not args.no_cpu and rank == 0:
+            w, opts = batch_oracle_sample()
+            line["cpu_baseline"] = oracle_baseline(w, opts)
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c5":
+        return main_batch(args)
     import torch
     from paper_1603_02524_gb300 import Grid, Hierarchy, binding
 
@@ -212,7 +390,9 @@ def main():
     lib = binding.load()
     w, opts = workload(args.workload)
     grid = Grid(w.dim, w.P, w.n_elem, w.spacing, periodic=w.periodic, mu_star=w.mu_star, beta=w.beta)
-    h = Hierarchy(grid, precision=args.precision, **opts)
+    h = Hierarchy(grid, precision=args.precision, outer_apply=args.outer_apply, **opts)
+    if args.autotune:
+        h.autotune()
     n = h.ndof()
     f = syn.source_values(w, [grid.coords(d) for d in range(w.dim)])
     ft = torch.from_numpy(f.reshape(-1)).to(dev)
@@ -252,9 +432,10 @@ def main():
     value = world * n / (t_step * 1e-3)
     line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "vs_baseline": None, "dtype": DTYPE[(args.precision, args.outer_apply)],
             "data": "synthetic",
             "config": {"workload": w.name, "dim": w.dim, "P": w.P, "n_elem": list(w.n_elem), "ndof": n,
+                       "precision": args.precision, "outer_apply": args.outer_apply, "autotune": args.autotune,
                        "smoother": opts["smoother"] + "_l", "flux": "IP" if w.beta == 0 else "LDG",
                        "rtol": 1e-10, "iterations": iters[0], "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas{world}"},
@@ -330,39 +511,79 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
     # apply kernel (FP64, the outer CG's operator): share of the solve
     r = torch.empty_like(g)
     ms_apply = time_kernel(lambda: h.apply(h.L, g, r), 10, stream, flush)
-    line["apply"] = {"ms": ms_apply, "gdof_s": n / (ms_apply * 1e-3) / 1e9, "dtype": "f64"}
-    # --- the other arithmetic on the same problem: mixed (fp32 V-cycle inside the FP64 CG) vs FP64
-    other = "mixed" if fp64_main else "fp64"
-    hm = Hierarchy(grid, precision=other, **opts)
-    um = torch.zeros_like(g)
-    for _ in range(1):
-        um.zero_()
-        hm.solve(g, um, rtol=1e-10, history=False)
-    tm, itm = [], 0
-    for _ in range(max(2, min(args.steps, 3))):
-        flush.fill_(1.0)
-        um.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rc, itm, _ = hm.solve(g, um, rtol=1e-10, history=False)
-        e1.record(stream)
-        e1.synchronize()
-        tm.append(e0.elapsed_time(e1))
+    line["apply"] = {"ms": ms_apply, "gdof_s": n / (ms_apply * 1e-3) / 1e9,
+                     "dtype": "f64" if args.outer_apply == "fp64" else "df32 (double-float)"}
+    if args.outer_apply == "fp64":        # the double-float apply on the same vectors
+        hdf = Hierarchy(grid, precision=args.precision, outer_apply="df", **opts)
+        r2 = torch.empty_like(g)
+        ms_df = time_kernel(lambda: hdf.apply(hdf.L, g, r2), 10, stream, flush)
+        line["apply"]["df_ms"] = ms_df
+        line["apply"]["df_speedup"] = ms_apply / ms_df
+        line["apply"]["df_max_rel_diff"] = float((r2 - r).abs().max() / r.abs().max())
+        hdf.close()
+    # --- the other arithmetics on the same problem: fp32 V-cycle inside the FP64 CG, with the
+    # patch transforms on the SIMT cores ("mixed") or the tensor cores ("mixed_tc"), vs FP64
+    others = [k for k, v in VARIANTS.items() if v != (args.precision, args.outer_apply)]
     u.zero_()
     h.solve(g, u, rtol=1e-10, history=False)
-    rel = float((um - u).abs().max() / u.abs().max())
-    ms_o = time_kernel(lambda: native(hm), 5, stream, flush)
-    t_o = statistics.mean(tm)
-    entry = {"value": n / (t_o * 1e-3), "unit": "DOF/s", "ms_per_step": t_o, "iterations": itm,
-             "status": rc, "max_rel_diff_between_solutions": rel, "patch_sweep_ms": ms_o}
-    if fp64_main:
-        entry["speedup_vs_fp64"] = line["ms_per_step"] / t_o
-        line["mixed"] = entry
-    else:
-        line["fp64_plain"] = entry
-        line["speedup_vs_fp64"] = t_o / line["ms_per_step"]
-    hm.close()
+    for other in others:
+        prec, outer = VARIANTS[other]
+        hm = Hierarchy(grid, precision=prec, outer_apply=outer, **opts)
+        um = torch.zeros_like(g)
+        hm.solve(g, um, rtol=1e-10, history=False)
+        tm, itm = [], 0
+        for _ in range(max(2, min(args.steps, 3))):
+            flush.fill_(1.0)
+            um.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc, itm, _ = hm.solve(g, um, rtol=1e-10, history=False)
+            e1.record(stream)
+            e1.synchronize()
+            tm.append(e0.elapsed_time(e1))
+        rel = float((um - u).abs().max() / u.abs().max())
+        ms_o = time_kernel(lambda: native(hm), 5, stream, flush)
+        t_o = statistics.mean(tm)
+        entry = {"value": n / (t_o * 1e-3), "unit": "DOF/s", "ms_per_step": t_o, "iterations": itm,
+                 "status": rc, "max_rel_diff_between_solutions": rel, "patch_sweep_ms": ms_o}
+        if other == "fp64_plain":
+            line["fp64_plain"] = entry
+            line["speedup_vs_fp64"] = t_o / line["ms_per_step"]
+        else:
+            t64 = line["fp64_plain"]["ms_per_step"] if "fp64_plain" in line else line["ms_per_step"]
+            entry["speedup_vs_fp64"] = t64 / t_o
+            line[other] = entry
+        hm.close()
+    # --- learned per-level smoother parameters (FA smoother): train on the library's own
+    # measured rates (generated 4^3-element grids), then solve this workload with them
+    if opts["smoother"] == "FA":
+        from paper_1603_02524_gb300 import learned
+        t0 = time.perf_counter()
+        net, hist, _ = learned.train_default()
+        t_train = time.perf_counter() - t0
+        om, ta = net.level_params(w.P, w.spacing)
+        hl = Hierarchy(grid, precision=args.precision, omega_level=om, tau_level=ta, **opts)
+        ul = torch.zeros_like(g)
+        hl.solve(g, ul, rtol=1e-10, history=False)
+        tl, itl = [], 0
+        for _ in range(max(2, min(args.steps, 3))):
+            flush.fill_(1.0)
+            ul.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rcl, itl, _ = hl.solve(g, ul, rtol=1e-10, history=False)
+            e1.record(stream)
+            e1.synchronize()
+            tl.append(e0.elapsed_time(e1))
+        line["learned"] = {"value": n / (statistics.mean(tl) * 1e-3), "unit": "DOF/s",
+                           "ms_per_step": statistics.mean(tl), "iterations": itl, "status": rcl,
+                           "paper_parameters_iterations": line["config"]["iterations"],
+                           "speedup_vs_paper_parameters": line["ms_per_step"] / statistics.mean(tl),
+                           "omega_level": om[1:], "tau_level": ta[1:], "training_s": t_train,
+                           "training_loss": [hist[0], hist[-1]]}
+        hl.close()
     # --- end to end through the host-buffer C-ABI call (pinned host memory)
     g_host = g.cpu().pin_memory()
     u_host = torch.zeros(n, dtype=torch.float64).pin_memory()

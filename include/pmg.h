@@ -20,8 +20,9 @@
  *    freed in pmg_hierarchy_destroy).
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Calls enqueue work on that stream and return without synchronising,
- *    except pmg_solve / pmg_solve_host, which synchronise once per CG
- *    iteration to test convergence.
+ *    except pmg_solve / pmg_solve_host / pmg_batch_solve, which synchronise
+ *    before returning (the first pmg_solve of a hierarchy once per CG
+ *    iteration, later ones and batches once per call).
  *  - Every call returns a pmg_status (0 = PMG_OK) and never throws.  Invalid
  *    arguments are rejected before any work is enqueued.  Kernel launch errors
  *    return PMG_ECUDA; numerical breakdown detected on the device returns
@@ -38,6 +39,7 @@ extern "C" {
 
 typedef struct pmg_grid_s* pmg_grid;
 typedef struct pmg_hier_s* pmg_hier;
+typedef struct pmg_batch_s* pmg_batch;
 
 typedef enum {
   PMG_OK = 0,
@@ -58,9 +60,20 @@ enum { PMG_OVERLAP_ZERO = 0, PMG_OVERLAP_LEVEL = 1, PMG_OVERLAP_LEVEL_FLOOR = 2 
 /* Weighting of the additive update, Eqs. (weight function:ec/fc). */
 enum { PMG_WEIGHT_UNWEIGHTED = 0, PMG_WEIGHT_ARITHMETIC = 1, PMG_WEIGHT_CUBIC = 3,
        PMG_WEIGHT_QUINTIC = 5 };
-/* Arithmetic of the V-cycle: FP64 everywhere, or FP32 V-cycle (smoother,
- * residuals, transfers) inside the FP64 flexible CG (spec extension). */
-enum { PMG_PREC_FP64 = 0, PMG_PREC_MIXED = 1 };
+/* Arithmetic of the V-cycle: FP64 everywhere; or an fp32 V-cycle (smoother,
+ * residuals, transfers) inside the FP64 flexible CG (spec extension), with
+ * the patch transforms on the SIMT cores (MIXED) or on the tensor cores (MIXED_TC:
+ * mma.sync TF32 with the 3xTF32 split, i.e. fp32-level products and fp32
+ * accumulation; 3-D patches of at most 32 nodes per axis, others stay SIMT). */
+enum { PMG_PREC_FP64 = 0, PMG_PREC_MIXED = 1, PMG_PREC_MIXED_TC = 2 };
+/* Preconditioner of the CG iteration (Algorithm 2). */
+enum { PMG_PC_VCYCLE = 0, PMG_PC_NONE = 1 };
+/* Arithmetic of the CG's operator apply (spec extension): FP64, or
+ * emulated FP64 in double-float (DF: each value the sum of two fp32 words,
+ * about 48 significant bits, products split exactly by FMA and sums by TwoSum)
+ * on the FP32 pipes, which on GB300 issue ~60x the FP64 rate.  DF needs the
+ * vector and operator magnitudes within fp32's exponent range (~1e-30..1e30). */
+enum { PMG_OUTER_FP64 = 0, PMG_OUTER_DF = 1 };
 
 typedef struct {
   int smoother;        /* PMG_SMOOTHER_*                                  (default EA) */
@@ -79,6 +92,10 @@ typedef struct {
    * partition of unity. */
   double omega_level[8];
   double tau_level[8];
+  int preconditioner;  /* PMG_PC_*: the V-cycle of Algorithm 1 (default), or none:
+                          z = r, i.e. plain CG, the paper's reference method of Sec. 4 */
+  int outer_apply;     /* PMG_OUTER_*: arithmetic of the CG's own operator apply
+                          (residual g - A u and q = A p of Algorithm 2) (default FP64) */
 } pmg_options;
 
 typedef struct {
@@ -86,6 +103,9 @@ typedef struct {
   double r0;           /* ||g - A u_0||_2                                    */
   double rn;           /* ||r|| at exit                                      */
   double* history;     /* optional host array of max_iter+1 entries, or NULL */
+  int status;          /* pmg_status of this solve (pmg_solve also returns it) */
+  int device_loop;     /* 1: the iterations ran as a device-side loop inside one
+                          CUDA graph launch; 0: host-driven iterations        */
 } pmg_stats;
 
 /* Fill *opt with the defaults listed above. */
@@ -132,10 +152,12 @@ void pmg_hierarchy_destroy(pmg_hier h);
 int pmg_num_levels(pmg_hier h);
 int pmg_level_info(pmg_hier h, int level, int* P_l, long long* ndof);
 
-/* Au_dev = A_l u_dev  (Eq. discrete problem; 3-D tensor form). level in 0..L. */
+/* Au_dev = A_l u_dev  (Eq. discrete problem; 3-D tensor form). level in 0..L.
+ * On the finest level L this is the CG's own apply, in the hierarchy's
+ * outer_apply arithmetic (FP64 by default); coarser levels are FP64. */
 int pmg_apply(pmg_hier h, int level, const double* u_dev, double* Au_dev, void* stream);
 
-/* r_dev = f_dev - A_l u_dev. */
+/* r_dev = f_dev - A_l u_dev (arithmetic as pmg_apply). */
 int pmg_residual(pmg_hier h, int level, const double* u_dev, const double* f_dev, double* r_dev,
                  void* stream);
 
@@ -204,6 +226,48 @@ int pmg_solve(pmg_hier h, const double* g_dev, double* u_dev, double rtol, pmg_s
  */
 int pmg_solve_host(pmg_hier h, const double* g_host, double* u_host, double rtol,
                    pmg_stats* stats, void* stream);
+
+/*
+ * Batched solves (spec extension; the paper solves one problem at a
+ * time).  pmg_batch_create records `count` independent MGCG solves (Algorithm
+ * 2), solve i on hierarchy hiers[i] with right-hand side g_dev[i] and initial
+ * guess / solution u_dev[i], into one CUDA graph: one branch per solve, each
+ * with its iterations in a device-side loop and its own convergence test
+ * ||r||_2 <= rtol ||r_0||_2 (cap: that hierarchy's max_iter).  Grids may differ
+ * in size, order, spacing and options; several right-hand sides of one grid
+ * need one hierarchy each (a hierarchy holds one solve's workspace), so the
+ * hierarchies must be distinct (else PMG_EINVAL).  The vectors are the
+ * caller's and are bound to the batch: pmg_batch_solve reads g_dev[i] and
+ * u_dev[i] where they are at that call.
+ *   pmg_batch_solve  runs all solves with one graph launch on `stream`,
+ *                    synchronises once, fills stats[0..count-1] (may be NULL;
+ *                    history arrays optional) and returns PMG_OK or the status
+ *                    of the first solve (by index) that failed.
+ *   pmg_batch_destroy  frees the graph; destroy a batch before its hierarchies.
+ * Creation runs one V-cycle on each hierarchy that has not run yet (kernel
+ * set-up) and synchronises the device.  Not thread safe with respect to the
+ * hierarchies it holds.
+ */
+int pmg_batch_create(int count, const pmg_hier* hiers, const double* const* g_dev,
+                     double* const* u_dev, double rtol, pmg_batch* out);
+int pmg_batch_solve(pmg_batch b, pmg_stats* stats, void* stream);
+void pmg_batch_destroy(pmg_batch b);
+/* Text of the last error recorded on a batch ("" if none). */
+const char* pmg_batch_last_error(pmg_batch b);
+
+/*
+ * Autotuner (spec extension): times the Schwarz patch kernel of every
+ * level with each candidate CTA size (multiples of 32 from 64 to 512) on the
+ * level's own work vectors and keeps the fastest; a line pass strides over its
+ * lines by the CTA size, so every candidate computes the same result.  Results
+ * are cached per patch shape and patch count for the process.  Enqueues on
+ * `stream` and synchronises it; overwrites the hierarchy's level work vectors.
+ * Call it before pmg_batch_create: a batch keeps the launch shapes it captured.
+ * pmg_tuned_threads returns the CTA size in use for (level >= 1, family as in
+ * pmg_schwarz_sweep), 0 = the kernel's default, or PMG_EINVAL.
+ */
+int pmg_hierarchy_autotune(pmg_hier h, void* stream);
+int pmg_tuned_threads(pmg_hier h, int level, int family);
 
 /*
  * One additive Schwarz sweep without the residual (Sec. 3.1, Eq.

@@ -6,7 +6,7 @@ holds its sources (``csrc/``), the build script and a thin ctypes binding.
 Nothing here falls back to a CPU implementation: without the built library every
 call raises.
 """
-from .binding import Grid, Hierarchy, PmgError, load  # noqa: F401
+from .binding import Batch, Grid, Hierarchy, PmgError, load  # noqa: F401
 
 __all__ = ["Grid", "Hierarchy", "PmgError", "load", "build"]
 

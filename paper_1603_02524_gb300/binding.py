@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libpmg.so")
 SMOOTHER = {"EA": 0, "FA": 1}
 OVERLAP = {"0": 0, "l": 1, "lf": 2}
 WEIGHTING = {"unweighted": 0, "arithmetic": 1, "cubic": 3, "quintic": 5}
-PRECISION = {"fp64": 0, "mixed": 1}
+PRECISION = {"fp64": 0, "mixed": 1, "mixed_tc": 2}
 
 STATUS = {0: "PMG_OK", -1: "PMG_EINVAL", -2: "PMG_ENOMEM", -3: "PMG_ECUDA", -4: "PMG_ENOCONV",
           -5: "PMG_EBREAKDOWN", -6: "PMG_ENAN", -7: "PMG_ETIMEOUT"}
@@ -27,19 +27,22 @@ EXPORTS = ["pmg_options_default", "pmg_grid_create", "pmg_grid_destroy", "pmg_gr
            "pmg_coarse_solve", "pmg_vcycle", "pmg_solve", "pmg_solve_host", "pmg_status_string",
            "pmg_last_error", "pmg_schwarz_sweep", "pmg_kernel_launches", "pmg_coarse_solve_static",
            "pmg_schwarz_sweep_fma", "pmg_schwarz_sweep_native", "pmg_mlp_forward",
-           "pmg_mlp_backward", "pmg_mlp_adam"]
+           "pmg_mlp_backward", "pmg_mlp_adam", "pmg_batch_create", "pmg_batch_solve",
+           "pmg_batch_destroy", "pmg_batch_last_error", "pmg_hierarchy_autotune", "pmg_tuned_threads"]
 
 
 class PmgOptions(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("overlap", ctypes.c_int), ("weighting", ctypes.c_int),
                 ("ns_pre", ctypes.c_int), ("ns_post", ctypes.c_int), ("variable_v", ctypes.c_int),
                 ("omega", ctypes.c_double), ("precision", ctypes.c_int), ("max_iter", ctypes.c_int),
-                ("omega_level", ctypes.c_double * 8), ("tau_level", ctypes.c_double * 8)]
+                ("omega_level", ctypes.c_double * 8), ("tau_level", ctypes.c_double * 8),
+                ("preconditioner", ctypes.c_int), ("outer_apply", ctypes.c_int)]
 
 
 class PmgStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("r0", ctypes.c_double), ("rn", ctypes.c_double),
-                ("history", ctypes.POINTER(ctypes.c_double))]
+                ("history", ctypes.POINTER(ctypes.c_double)), ("status", ctypes.c_int),
+                ("device_loop", ctypes.c_int)]
 
 
 class PmgError(RuntimeError):
@@ -93,6 +96,12 @@ def load(path: str | None = None):
         "pmg_mlp_backward": (i, [vp, vp, vp, vp, vp, vp, vp, i, vp, vp, vp, vp]),
         "pmg_mlp_adam": (i, [vp, vp, vp, vp, i, i, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                              ctypes.c_float, vp]),
+        "pmg_batch_create": (i, [i, vp, vp, vp, d, vp]),
+        "pmg_batch_solve": (i, [vp, ctypes.POINTER(PmgStats), vp]),
+        "pmg_batch_destroy": (None, [vp]),
+        "pmg_batch_last_error": (ctypes.c_char_p, [vp]),
+        "pmg_hierarchy_autotune": (i, [vp, vp]),
+        "pmg_tuned_threads": (i, [vp, i, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -103,8 +112,11 @@ def load(path: str | None = None):
 
 
 def options(smoother="EA", overlap="l", weighting="quintic", ns=(1, 1), variable_v=False,
-            omega=1.0, precision="fp64", max_iter=100, omega_level=None, tau_level=None) -> PmgOptions:
-    """omega_level / tau_level: optional per-level sequences (index = level, 0 = default)."""
+            omega=1.0, precision="fp64", max_iter=100, omega_level=None, tau_level=None,
+            preconditioner="vcycle", outer_apply="fp64") -> PmgOptions:
+    """omega_level / tau_level: optional per-level sequences (index = level, 0 = default);
+    preconditioner "vcycle" (Algorithm 2) or "none" (plain CG); outer_apply "fp64" or "df"
+    (the CG's operator apply in double-float on the FP32 pipes)."""
     o = PmgOptions()
     load().pmg_options_default(ctypes.byref(o))
     o.smoother = SMOOTHER[smoother]
@@ -119,6 +131,8 @@ def options(smoother="EA", overlap="l", weighting="quintic", ns=(1, 1), variable
         o.omega_level[l] = float(v)
     for l, v in enumerate(tau_level or []):
         o.tau_level[l] = float(v)
+    o.preconditioner = {"vcycle": 0, "none": 1}[preconditioner]
+    o.outer_apply = {"fp64": 0, "df": 1}[outer_apply]
     return o
 
 
@@ -260,6 +274,7 @@ class Hierarchy:
         rc = load().pmg_solve(self.handle, _dev(g, n), _dev(u, n), float(rtol), ctypes.byref(st), _stream(stream))
         if check and rc not in (0, -4):
             _check("pmg_solve", rc, self.handle)
+        self.last_device_loop = bool(st.device_loop)
         h = list(hist[: st.iterations + 1]) if history else []
         return rc, st.iterations, h
 
@@ -282,9 +297,75 @@ class Hierarchy:
             _check("pmg_solve_host", rc, self.handle)
         return rc, st.iterations
 
+    def autotune(self, stream=None):
+        """Pick the patch kernel's CTA size per level by timing (pmg_hierarchy_autotune)."""
+        _check("pmg_hierarchy_autotune", load().pmg_hierarchy_autotune(self.handle, _stream(stream)),
+               self.handle)
+
+    def tuned_threads(self, level, family=-1):
+        st = load().pmg_tuned_threads(self.handle, level, family)
+        if st < 0:
+            _check("pmg_tuned_threads", st, self.handle)
+        return st
+
     def close(self):
         if getattr(self, "handle", None):
             load().pmg_hierarchy_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """pmg_batch_create / pmg_batch_solve / pmg_batch_destroy: independent MGCG solves
+    (one per distinct hierarchy, with its own g and u device tensors) recorded as one
+    CUDA graph and run with one launch."""
+
+    def __init__(self, hiers, gs, us, rtol=1e-10):
+        lib = load()
+        n = len(hiers)
+        if not (n == len(gs) == len(us)) or n == 0:
+            raise ValueError("hiers, gs and us must have the same non-zero length")
+        self._keep = (list(hiers), list(gs), list(us))
+        hs = (ctypes.c_void_p * n)(*[h.handle.value for h in hiers])
+        gp = (ctypes.c_void_p * n)(*[_dev(g, h.ndof()).value for g, h in zip(gs, hiers)])
+        up = (ctypes.c_void_p * n)(*[_dev(u, h.ndof()).value for u, h in zip(us, hiers)])
+        b = ctypes.c_void_p()
+        _check("pmg_batch_create", lib.pmg_batch_create(n, hs, gp, up, float(rtol), ctypes.byref(b)))
+        self.handle = b
+        self.count = n
+        self.max_iter = [h.opts.max_iter for h in hiers]
+
+    def solve(self, stream=None, history=False, check=True):
+        """Run every solve; returns (status, [(status, iterations, r0, rn[, history]) ...])."""
+        st = (PmgStats * self.count)()
+        hists = []
+        for i in range(self.count):
+            if history:
+                hist = (ctypes.c_double * (self.max_iter[i] + 1))()
+                hists.append(hist)
+                st[i].history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+            else:
+                st[i].history = None
+        rc = load().pmg_batch_solve(self.handle, st, _stream(stream))
+        if check and rc not in (0, -4):
+            detail = (load().pmg_batch_last_error(self.handle) or b"").decode()
+            raise PmgError("pmg_batch_solve", rc, detail)
+        out = []
+        for i in range(self.count):
+            item = (st[i].status, st[i].iterations, st[i].r0, st[i].rn)
+            if history:
+                item = item + (list(hists[i][: st[i].iterations + 1]),)
+            out.append(item)
+        return rc, out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pmg_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -1,0 +1,211 @@
+// Sum-factorised DG operator apply (shared by the FP64 / fp32 library
+// kernels and the double-float outer apply).
+//
+// Paper: Stiller, arXiv 1603.02524, Sec. 2.4 (1-D blocks of Eq. L:generic) and
+// the tensor form of the discrete problem (Sec. 2.2, reading C1 in 3-D).
+#pragma once
+
+#include "pmg_internal.h"
+
+namespace pmg {
+
+// table / vector loads through the read-only path (dfloat: one 8-byte load)
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// c + a * b, fused (dfloat: the accumulate form of dfloat.cuh)
+__device__ __forceinline__ double madd(double a, double b, double c) { return ::fma(a, b, c); }
+__device__ __forceinline__ float madd(float a, float b, float c) { return fmaf(a, b, c); }
+
+// Allow `bytes` of dynamic shared memory for kernel `fn` (once per kernel).
+template <typename K>
+static bool set_smem(K fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return true;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+         cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Operator apply: v = A u or v = f - A u  (Eq. discrete problem, 3-D tensor form)
+//
+// One thread owns one nodal line of one element per axis pass.  The element is
+// staged in shared memory; the line is contracted with the element's dense
+// 1-D block L^0 (Eq. L:generic); the neighbour blocks L^-/L^+ have rank <= 3
+// and need only the neighbour line's end value and end derivative
+// (sum_k D_{P,k} u_k^{m-1}, sum_k D_{0,k} u_k^{m+1}), which the thread reads
+// from global memory (L2-resident: neighbouring CTAs read the same elements).
+// Each pass result is scaled by the diagonal masses of the two other axes and
+// accumulated in shared memory.
+// ---------------------------------------------------------------------------
+template <int DIM, int NP>
+struct ApplyShape {
+  static constexpr int LINES = (DIM == 3) ? NP * NP : NP;
+  static constexpr int NODES = (DIM == 3) ? NP * NP * NP : NP * NP;
+  static constexpr int EPB = (128 / LINES) > 0 ? (128 / LINES) : 1;
+  static constexpr int THREADS = ((EPB * LINES + 31) / 32) * 32;
+  // CTAs per SM the register budget must allow (8-byte types): two for the 3-D
+  // P = 16 kernel (320 threads), whose double-float form would otherwise take 114
+  // registers and run one CTA per SM
+  static constexpr int MINB8 = (DIM == 3 && NP == 17) ? 2 : 0;
+};
+
+// T: arithmetic and table type; TIO: type of u, f, v in global memory.
+template <typename T, int DIM, int NP, bool RESIDUAL, typename TIO = T>
+__global__ void __launch_bounds__(ApplyShape<DIM, NP>::THREADS, sizeof(T) == 8 ? ApplyShape<DIM, NP>::MINB8 : 0)
+apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const TIO* __restrict__ f,
+             TIO* __restrict__ v) {
+  using S = ApplyShape<DIM, NP>;
+  constexpr int P = NP - 1;
+  extern __shared__ __align__(16) unsigned char apply_smem[];
+  T* su = reinterpret_cast<T*>(apply_smem);
+  T* acc = su + S::EPB * S::NODES;
+  const int tid = threadIdx.x;
+  const long long e0 = (long long)blockIdx.x * S::EPB;
+  const long long nodes_blk = (long long)S::EPB * S::NODES;
+  const long long total = dm.nelem * S::NODES;
+  for (int t = tid; t < nodes_blk; t += blockDim.x) {
+    long long g = e0 * S::NODES + t;
+    su[t] = g < total ? T(u[g]) : T(0);
+  }
+  __syncthreads();
+  const int el = tid / S::LINES;
+  const int line = tid % S::LINES;
+  const long long e = e0 + el;
+  const bool active = (el < S::EPB) && (e < dm.nelem);
+  int me[3] = {0, 0, 0};
+  if (active) {
+    me[0] = (int)(e % dm.ne[0]);
+    me[1] = (int)((e / dm.ne[0]) % dm.ne[1]);
+    me[2] = (int)(e / ((long long)dm.ne[0] * dm.ne[1]));
+  }
+  T* sel = su + el * S::NODES;
+  T* ael = acc + el * S::NODES;
+  constexpr int H = NP / 2, NE = NP - H, NO = H;
+#pragma unroll 1
+  for (int d = 0; d < DIM; ++d) {
+    if (active) {
+      int off, stride;
+      if (DIM == 3) {
+        if (d == 0) { off = line * NP; stride = 1; }
+        else if (d == 1) { off = (line / NP) * NP * NP + line % NP; stride = NP; }
+        else { off = line; stride = NP * NP; }
+      } else {
+        if (d == 0) { off = line * NP; stride = 1; }
+        else { off = line; stride = NP; }
+      }
+      T x[NP], y[NP];
+#pragma unroll
+      for (int a = 0; a < NP; ++a) x[a] = sel[off + a * stride];
+      const T* L0 = at.L0[d] + (size_t)me[d] * NP * NP;
+      if (__ldg(at.sym[d] + me[d])) {
+        // even-odd split of the centro-symmetric block (folded table layout)
+        T xp[NE], xm[NO > 0 ? NO : 1];
+#pragma unroll
+        for (int a = 0; a < H; ++a) {
+          xp[a] = x[a] + x[P - a];
+          xm[a] = x[a] - x[P - a];
+        }
+        if (NE > H) xp[NE - 1] = x[H];
+        const T* E = L0;
+        const T* O = L0 + NE * NE;
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+          T e = T(0), o = T(0);
+#pragma unroll
+          for (int a = 0; a < NE; ++a) e = madd(ldg(E + i * NE + a), xp[a], e);
+#pragma unroll
+          for (int a = 0; a < NO; ++a) o = madd(ldg(O + i * NO + a), xm[a], o);
+          y[i] = e + o;
+          y[P - i] = e - o;
+        }
+        if (NE > H) {
+          T e = T(0);
+#pragma unroll
+          for (int a = 0; a < NE; ++a) e = madd(ldg(E + H * NE + a), xp[a], e);
+          y[H] = e;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          T s = T(0);
+#pragma unroll
+          for (int a = 0; a < NP; ++a) s = madd(ldg(L0 + i * NP + a), x[a], s);
+          y[i] = s;
+        }
+      }
+      // neighbour blocks L^-, L^+ (rank <= 3, already scaled by M_d^-1)
+      const T* c = at.cpl[d] + (size_t)me[d] * (2 * NP + 8);
+      const long long estride = (d == 0) ? 1 : (d == 1 ? (long long)dm.ne[0] : (long long)dm.ne[0] * dm.ne[1]);
+      const int ned = dm.ne[d];
+      if (ldg(c + 2 * NP + 2) != T(0)) {          // neighbour m-1 exists
+        long long en = (me[d] > 0) ? e - estride : e + (long long)(ned - 1) * estride;
+        const TIO* un = u + en * S::NODES + off;
+        T uP = T(0), dP = T(0);
+#pragma unroll
+        for (int a = 0; a < NP; ++a) {
+          T val = T(__ldg(un + a * stride));
+          dP = madd(ldg(at.DP + a), val, dP);
+          if (a == P) uP = val;
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) y[i] = madd(ldg(c + i), uP, y[i]);
+        y[0] += ldg(c + 2 * NP + 0) * dP - ldg(c + 2 * NP + 1) * uP;
+      }
+      if (ldg(c + 2 * NP + 5) != T(0)) {          // neighbour m+1 exists
+        long long en = (me[d] < ned - 1) ? e + estride : e - (long long)(ned - 1) * estride;
+        const TIO* un = u + en * S::NODES + off;
+        T u0 = T(0), d0 = T(0);
+#pragma unroll
+        for (int a = 0; a < NP; ++a) {
+          T val = T(__ldg(un + a * stride));
+          d0 = madd(ldg(at.D0 + a), val, d0);
+          if (a == 0) u0 = val;
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) y[i] = madd(ldg(c + NP + i), u0, y[i]);
+        y[P] = y[P] - (ldg(c + 2 * NP + 3) * d0 + ldg(c + 2 * NP + 4) * u0);
+      }
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        if (d == 0) ael[off + i * stride] = y[i];
+        else ael[off + i * stride] += y[i];
+      }
+    }
+    __syncthreads();
+  }
+  // v = (M_z (x) M_y (x) M_x) * (sum over axes of M_d^-1 L_d u)
+  for (int t = tid; t < nodes_blk; t += blockDim.x) {
+    long long g = e0 * S::NODES + t;
+    if (g >= total) continue;
+    const long long ee = g / S::NODES;
+    const int nd = (int)(g % S::NODES);
+    const int i = nd % NP, j = (nd / NP) % NP;
+    const int mx = (int)(ee % dm.ne[0]), my = (int)((ee / dm.ne[0]) % dm.ne[1]);
+    T m = ldg(at.M[0] + (size_t)mx * NP + i) * ldg(at.M[1] + (size_t)my * NP + j);
+    if (DIM == 3) {
+      const int k = nd / (NP * NP);
+      const int mz = (int)(ee / ((long long)dm.ne[0] * dm.ne[1]));
+      m = m * ldg(at.M[2] + (size_t)mz * NP + k);
+    }
+    const T val = m * acc[t];
+    v[g] = RESIDUAL ? TIO(T(f[g]) - val) : TIO(val);
+  }
+}
+
+template <typename T, int DIM, int NP, typename TIO = T>
+static int apply_dispatch(const LevelDims& dm, const ApplyTables<T>& at, const TIO* u, const TIO* f,
+                          TIO* v, cudaStream_t s) {
+  using S = ApplyShape<DIM, NP>;
+  long long blocks = (dm.nelem + S::EPB - 1) / S::EPB;
+  const size_t smem = 2 * sizeof(T) * S::EPB * S::NODES;
+  if (f) {
+    if (!set_smem(apply_kernel<T, DIM, NP, true, TIO>, smem)) return PMG_ECUDA;
+    count_launch(); apply_kernel<T, DIM, NP, true, TIO><<<(unsigned)blocks, S::THREADS, smem, s>>>(dm, at, u, f, v);
+  } else {
+    if (!set_smem(apply_kernel<T, DIM, NP, false, TIO>, smem)) return PMG_ECUDA;
+    count_launch(); apply_kernel<T, DIM, NP, false, TIO><<<(unsigned)blocks, S::THREADS, smem, s>>>(dm, at, u, f, v);
+  }
+  return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
+}
+
+}  // namespace pmg

@@ -4,8 +4,15 @@
 
 namespace pmg {
 
+int fdm_dispatch_f3tc(const LevelDims& dm, const FdmFamily<float>& fam, const float* r, float* u,
+                      cudaStream_t s);
+
 int fdm_dispatch_f3(const LevelDims& dm, const FdmFamily<float>& fam, const float* r, float* u,
                      cudaStream_t s) {
+  if (fam.tc) {                    // tensor-core line passes (tables unfolded)
+    const int st = fdm_dispatch_f3tc(dm, fam, r, u, s);
+    if (st != PMG_EINVAL) return st;
+  }
   const int na = fam.ax[0].n, nb = fam.ax[1].n, nc = fam.ax[2].n;
 #define C(A, B, CC) \
   if (na == A && nb == B && nc == CC) return fdm_launch<float, A, B, CC>(dm, fam, r, u, s);

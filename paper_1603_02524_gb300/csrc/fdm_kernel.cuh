@@ -161,6 +161,106 @@ __device__ __forceinline__ void load_table(T* dst, const T* src, bool sym) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core line passes (fp32 data): out[line][n] = sum_k in[line][k] M[k][n]
+// as 16 x 8 x 8 tf32 MMAs with fp32 accumulation.  Each operand is split as
+// x = hi + lo with hi, lo tf32 and the product taken as hi*hi + hi*lo + lo*hi
+// (3xTF32), which keeps fp32-level accuracy.  M is the zero-padded table in
+// shared memory (P8 x P8, P8 = N rounded up to 8).  A warp owns 16 lines at a
+// time; it reads all N inputs of its lines before writing any output, so the
+// pass is in place.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned to_tf32(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int N>
+__device__ __forceinline__ void line_pass_mma(float* buf, const float* M, int nlines, int lo_stride,
+                                              int lo_count, int hi_stride, int stride) {
+  constexpr int P8 = (N + 7) / 8 * 8, KT = P8 / 8, NT = P8 / 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  // B fragments of the whole table (b0: row k = 8 kt + t, b1: row k + 4; column n = 8 nt + g)
+  unsigned bh[KT][NT][2], bl[KT][NT][2];
+#pragma unroll
+  for (int kt = 0; kt < KT; ++kt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const float b = M[(kt * 8 + t + 4 * j) * P8 + nt * 8 + g];
+        bh[kt][nt][j] = to_tf32(b);
+        bl[kt][nt][j] = to_tf32(b - __uint_as_float(bh[kt][nt][j]));
+      }
+  const int mtiles = (nlines + 15) / 16;
+  for (int mt = warp; mt < mtiles; mt += nwarps) {
+    const int l0 = mt * 16 + g, l1 = l0 + 8;
+    const bool v0 = l0 < nlines, v1 = l1 < nlines;
+    const int b0 = v0 ? (l0 % lo_count) * lo_stride + (l0 / lo_count) * hi_stride : 0;
+    const int b1 = v1 ? (l1 % lo_count) * lo_stride + (l1 / lo_count) * hi_stride : 0;
+    float acc[NT][4];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+#pragma unroll
+    for (int kt = 0; kt < KT; ++kt) {
+      const int k0 = kt * 8 + t, k1 = k0 + 4;
+      // A fragment: (row g, col t), (row g+8, col t), (row g, col t+4), (row g+8, col t+4)
+      const float x[4] = {(v0 && k0 < N) ? buf[b0 + k0 * stride] : 0.0f,
+                          (v1 && k0 < N) ? buf[b1 + k0 * stride] : 0.0f,
+                          (v0 && k1 < N) ? buf[b0 + k1 * stride] : 0.0f,
+                          (v1 && k1 < N) ? buf[b1 + k1 * stride] : 0.0f};
+      unsigned ah[4], al[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ah[i] = to_tf32(x[i]);
+        al[i] = to_tf32(x[i] - __uint_as_float(ah[i]));
+      }
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        mma_tf32(acc[nt], al, bh[kt][nt][0], bh[kt][nt][1]);
+        mma_tf32(acc[nt], ah, bl[kt][nt][0], bl[kt][nt][1]);
+        mma_tf32(acc[nt], ah, bh[kt][nt][0], bh[kt][nt][1]);
+      }
+    }
+    __syncwarp();
+    // C fragment: (row g, cols 2t, 2t+1), (row g+8, cols 2t, 2t+1)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      const int n0 = nt * 8 + 2 * t;
+      if (v0 && n0 < N) buf[b0 + n0 * stride] = acc[nt][0];
+      if (v0 && n0 + 1 < N) buf[b0 + (n0 + 1) * stride] = acc[nt][1];
+      if (v1 && n0 < N) buf[b1 + n0 * stride] = acc[nt][2];
+      if (v1 && n0 + 1 < N) buf[b1 + (n0 + 1) * stride] = acc[nt][3];
+    }
+    __syncwarp();
+  }
+}
+
+// Zero-padded P8 x P8 copy of an n x n table for the tensor-core passes.
+template <int N>
+__device__ __forceinline__ void load_table_mma(float* dst, const float* src) {
+  constexpr int P8 = (N + 7) / 8 * 8;
+  for (int t = threadIdx.x; t < P8 * P8; t += blockDim.x) {
+    const int r = t / P8, c = t % P8;
+    dst[t] = (r < N && c < N) ? src[r * N + c] : 0.0f;
+  }
+}
+
+template <typename T, bool TC>
+__host__ __device__ constexpr int table_floats(int n) {
+  return TC ? (n + 7) / 8 * 8 * ((n + 7) / 8 * 8) : n * padded<T>(n);
+}
+
 // 1 / s: hardware single-precision reciprocal refined by Newton's iteration
 // x <- x (2 - s x), written as x <- x + x (1 - s x); each step squares the
 // relative error (2^-23 -> 2^-46 -> below double rounding).
@@ -173,8 +273,8 @@ __device__ __forceinline__ double recip(double s) {
 }
 __device__ __forceinline__ float recip(float s) { return __frcp_rn(s); }
 
-// CTA size: enough threads for the widest line pass (one line per thread),
-// rounded to whole warps, at most 256.
+// Default CTA size: enough threads for the widest line pass (one line per
+// thread), rounded to whole warps, at most 256.
 template <int NA, int NB, int NC>
 constexpr int fdm_threads() {
   constexpr int l0 = NB * NC, l1 = NA * NC, l2 = NA * NB;
@@ -183,9 +283,28 @@ constexpr int fdm_threads() {
   return t < 256 ? t : 256;
 }
 
-template <typename T, int NA, int NB, int NC>
-__global__ void __launch_bounds__(fdm_threads<NA, NB, NC>())
+// One line pass along an axis: tensor cores (fp32, TC) or SIMT (general / even-odd).
+template <typename T, int N, bool FORWARD, bool TC>
+__device__ __forceinline__ void pass(bool sym, T* buf, const T* M, int nlines, int lo_stride, int lo_count,
+                                     int hi_stride, int stride) {
+  if constexpr (TC) {
+    line_pass_mma<N>(buf, M, nlines, lo_stride, lo_count, hi_stride, stride);
+  } else {
+    axis_pass<T, N, FORWARD>(sym, buf, M, nlines, lo_stride, lo_count, hi_stride, stride);
+  }
+}
+
+template <typename T, int N, bool TC>
+__device__ __forceinline__ void tload(T* dst, const T* src, bool sym) {
+  if constexpr (TC) load_table_mma<N>(dst, src);
+  else load_table<T, N>(dst, src, sym);
+}
+
+template <typename T, int NA, int NB, int NC, bool TC>
+__global__ void __launch_bounds__(kFdmMaxThreads)
 fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restrict__ u) {
+  static_assert(!TC || (sizeof(T) == 4 && NA <= 32 && NB <= 32 && NC <= 32 && NC > 1),
+                "tensor-core passes: fp32, 3-D, at most 32 nodes per axis");
   constexpr int NN = NA * NB * NC;
   extern __shared__ __align__(16) unsigned char fdm_smem[];
   long long* off = reinterpret_cast<long long*>(fdm_smem);        // NA + NB + NC
@@ -193,12 +312,12 @@ fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restric
   T* Sq[3];
   T* Wq[3];
   Sq[0] = buf + padded<T>(NN);
-  Wq[0] = Sq[0] + NA * padded<T>(NA);
-  Sq[1] = Wq[0] + NA * padded<T>(NA);
-  Wq[1] = Sq[1] + NB * padded<T>(NB);
-  Sq[2] = Wq[1] + NB * padded<T>(NB);
-  Wq[2] = Sq[2] + NC * padded<T>(NC);
-  T* la = Wq[2] + NC * padded<T>(NC);
+  Wq[0] = Sq[0] + table_floats<T, TC>(NA);
+  Sq[1] = Wq[0] + table_floats<T, TC>(NA);
+  Wq[1] = Sq[1] + table_floats<T, TC>(NB);
+  Sq[2] = Wq[1] + table_floats<T, TC>(NB);
+  Wq[2] = Sq[2] + table_floats<T, TC>(NC);
+  T* la = Wq[2] + table_floats<T, TC>(NC);
   T* lb = la + NA;
   T* lc = lb + NB;
 
@@ -220,14 +339,14 @@ fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restric
     const size_t p = pidx[q];
     sym[q] = ax.sym[p] != 0;
     if (q == 0) {
-      load_table<T, NA>(Sq[0], ax.S + p * n * n, sym[0]);
-      load_table<T, NA>(Wq[0], ax.W + p * n * n, sym[0]);
+      tload<T, NA, TC>(Sq[0], ax.S + p * n * n, sym[0]);
+      tload<T, NA, TC>(Wq[0], ax.W + p * n * n, sym[0]);
     } else if (q == 1) {
-      load_table<T, NB>(Sq[1], ax.S + p * n * n, sym[1]);
-      load_table<T, NB>(Wq[1], ax.W + p * n * n, sym[1]);
+      tload<T, NB, TC>(Sq[1], ax.S + p * n * n, sym[1]);
+      tload<T, NB, TC>(Wq[1], ax.W + p * n * n, sym[1]);
     } else {
-      load_table<T, NC>(Sq[2], ax.S + p * n * n, sym[2]);
-      load_table<T, NC>(Wq[2], ax.W + p * n * n, sym[2]);
+      tload<T, NC, TC>(Sq[2], ax.S + p * n * n, sym[2]);
+      tload<T, NC, TC>(Wq[2], ax.W + p * n * n, sym[2]);
     }
     if (threadIdx.x < n) {
       const int a = threadIdx.x;
@@ -259,12 +378,12 @@ fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restric
   __syncthreads();
 
   // forward transforms
-  axis_pass<T, NA, true>(sym[0], buf, Sq[0], NB * NC, NA, NB * NC, 0, 1);
+  pass<T, NA, true, TC>(sym[0], buf, Sq[0], NB * NC, NA, NB * NC, 0, 1);
   __syncthreads();
-  axis_pass<T, NB, true>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA);
+  pass<T, NB, true, TC>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA);
   __syncthreads();
   if (NC > 1) {
-    axis_pass<T, NC, true>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB);
+    pass<T, NC, true, TC>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB);
     __syncthreads();
   }
   for (int t = threadIdx.x; t < NN; t += blockDim.x) {
@@ -273,12 +392,12 @@ fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restric
   }
   __syncthreads();
   if (NC > 1) {
-    axis_pass<T, NC, false>(sym[2], buf, Wq[2], NA * NB, 1, NA * NB, 0, NA * NB);
+    pass<T, NC, false, TC>(sym[2], buf, Wq[2], NA * NB, 1, NA * NB, 0, NA * NB);
     __syncthreads();
   }
-  axis_pass<T, NB, false>(sym[1], buf, Wq[1], NA * NC, 1, NA, NA * NB, NA);
+  pass<T, NB, false, TC>(sym[1], buf, Wq[1], NA * NC, 1, NA, NA * NB, NA);
   __syncthreads();
-  axis_pass<T, NA, false>(sym[0], buf, Wq[0], NB * NC, NA, NB * NC, 0, 1);
+  pass<T, NA, false, TC>(sym[0], buf, Wq[0], NB * NC, NA, NB * NC, 0, 1);
   __syncthreads();
 
   for (int t = threadIdx.x; t < NN; t += blockDim.x) {
@@ -288,27 +407,30 @@ fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restric
   }
 }
 
-template <typename T, int NA, int NB, int NC>
+template <typename T, int NA, int NB, int NC, bool TC>
 constexpr size_t fdm_smem_bytes() {
   return sizeof(long long) * ((NA + NB + NC + 1) / 2 * 2) +
          sizeof(T) * ((size_t)padded<T>(NA * NB * NC) +
-                      2 * (NA * padded<T>(NA) + NB * padded<T>(NB) + NC * padded<T>(NC)) + NA + NB + NC);
+                      2 * (table_floats<T, TC>(NA) + table_floats<T, TC>(NB) + table_floats<T, TC>(NC)) +
+                      NA + NB + NC);
 }
 
-template <typename T, int NA, int NB, int NC>
+template <typename T, int NA, int NB, int NC, bool TC = false>
 int fdm_launch(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, cudaStream_t s) {
-  constexpr size_t smem = fdm_smem_bytes<T, NA, NB, NC>();
+  constexpr size_t smem = fdm_smem_bytes<T, NA, NB, NC, TC>();
   static_assert(smem <= 227 * 1024, "patch does not fit in shared memory");
   static bool attr_done = false;
   if (!attr_done && smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(fdm_kernel<T, NA, NB, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(fdm_kernel<T, NA, NB, NC, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return PMG_ECUDA;
   }
   attr_done = true;
   if (fam.count_total <= 0) return PMG_OK;
+  const int threads = (fam.threads >= 32 && fam.threads <= kFdmMaxThreads && fam.threads % 32 == 0)
+                          ? fam.threads : fdm_threads<NA, NB, NC>();
   count_launch();
-  fdm_kernel<T, NA, NB, NC><<<fam.count_total, fdm_threads<NA, NB, NC>(), smem, s>>>(dm, fam, r, u);
+  fdm_kernel<T, NA, NB, NC, TC><<<fam.count_total, threads, smem, s>>>(dm, fam, r, u);
   return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
 }
 

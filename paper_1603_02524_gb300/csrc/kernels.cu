@@ -8,195 +8,9 @@
 
 #include <cooperative_groups.h>
 
-#include "pmg_internal.h"
+#include "apply_kernel.cuh"
 
 namespace pmg {
-
-// Allow `bytes` of dynamic shared memory for kernel `fn` (once per kernel).
-template <typename K>
-static bool set_smem(K fn, size_t bytes) {
-  if (bytes <= 48 * 1024) return true;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
-         cudaSuccess;
-}
-
-// ---------------------------------------------------------------------------
-// Operator apply: v = A u or v = f - A u  (Eq. discrete problem, 3-D tensor form)
-//
-// One thread owns one nodal line of one element per axis pass.  The element is
-// staged in shared memory; the line is contracted with the element's dense
-// 1-D block L^0 (Eq. L:generic); the neighbour blocks L^-/L^+ have rank <= 3
-// and need only the neighbour line's end value and end derivative
-// (sum_k D_{P,k} u_k^{m-1}, sum_k D_{0,k} u_k^{m+1}), which the thread reads
-// from global memory (L2-resident: neighbouring CTAs read the same elements).
-// Each pass result is scaled by the diagonal masses of the two other axes and
-// accumulated in shared memory.
-// ---------------------------------------------------------------------------
-template <int DIM, int NP>
-struct ApplyShape {
-  static constexpr int LINES = (DIM == 3) ? NP * NP : NP;
-  static constexpr int NODES = (DIM == 3) ? NP * NP * NP : NP * NP;
-  static constexpr int EPB = (128 / LINES) > 0 ? (128 / LINES) : 1;
-  static constexpr int THREADS = ((EPB * LINES + 31) / 32) * 32;
-};
-
-template <typename T, int DIM, int NP, bool RESIDUAL>
-__global__ void __launch_bounds__(ApplyShape<DIM, NP>::THREADS)
-apply_kernel(LevelDims dm, ApplyTables<T> at, const T* __restrict__ u, const T* __restrict__ f,
-             T* __restrict__ v) {
-  using S = ApplyShape<DIM, NP>;
-  constexpr int P = NP - 1;
-  extern __shared__ __align__(16) unsigned char apply_smem[];
-  T* su = reinterpret_cast<T*>(apply_smem);
-  T* acc = su + S::EPB * S::NODES;
-  const int tid = threadIdx.x;
-  const long long e0 = (long long)blockIdx.x * S::EPB;
-  const long long nodes_blk = (long long)S::EPB * S::NODES;
-  const long long total = dm.nelem * S::NODES;
-  for (int t = tid; t < nodes_blk; t += blockDim.x) {
-    long long g = e0 * S::NODES + t;
-    su[t] = g < total ? u[g] : T(0);
-  }
-  __syncthreads();
-  const int el = tid / S::LINES;
-  const int line = tid % S::LINES;
-  const long long e = e0 + el;
-  const bool active = (el < S::EPB) && (e < dm.nelem);
-  int me[3] = {0, 0, 0};
-  if (active) {
-    me[0] = (int)(e % dm.ne[0]);
-    me[1] = (int)((e / dm.ne[0]) % dm.ne[1]);
-    me[2] = (int)(e / ((long long)dm.ne[0] * dm.ne[1]));
-  }
-  T* sel = su + el * S::NODES;
-  T* ael = acc + el * S::NODES;
-  constexpr int H = NP / 2, NE = NP - H, NO = H;
-#pragma unroll 1
-  for (int d = 0; d < DIM; ++d) {
-    if (active) {
-      int off, stride;
-      if (DIM == 3) {
-        if (d == 0) { off = line * NP; stride = 1; }
-        else if (d == 1) { off = (line / NP) * NP * NP + line % NP; stride = NP; }
-        else { off = line; stride = NP * NP; }
-      } else {
-        if (d == 0) { off = line * NP; stride = 1; }
-        else { off = line; stride = NP; }
-      }
-      T x[NP], y[NP];
-#pragma unroll
-      for (int a = 0; a < NP; ++a) x[a] = sel[off + a * stride];
-      const T* L0 = at.L0[d] + (size_t)me[d] * NP * NP;
-      if (__ldg(at.sym[d] + me[d])) {
-        // even-odd split of the centro-symmetric block (folded table layout)
-        T xp[NE], xm[NO > 0 ? NO : 1];
-#pragma unroll
-        for (int a = 0; a < H; ++a) {
-          xp[a] = x[a] + x[P - a];
-          xm[a] = x[a] - x[P - a];
-        }
-        if (NE > H) xp[NE - 1] = x[H];
-        const T* E = L0;
-        const T* O = L0 + NE * NE;
-#pragma unroll
-        for (int i = 0; i < H; ++i) {
-          T e = T(0), o = T(0);
-#pragma unroll
-          for (int a = 0; a < NE; ++a) e = fma(__ldg(E + i * NE + a), xp[a], e);
-#pragma unroll
-          for (int a = 0; a < NO; ++a) o = fma(__ldg(O + i * NO + a), xm[a], o);
-          y[i] = e + o;
-          y[P - i] = e - o;
-        }
-        if (NE > H) {
-          T e = T(0);
-#pragma unroll
-          for (int a = 0; a < NE; ++a) e = fma(__ldg(E + H * NE + a), xp[a], e);
-          y[H] = e;
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          T s = T(0);
-#pragma unroll
-          for (int a = 0; a < NP; ++a) s = fma(__ldg(L0 + i * NP + a), x[a], s);
-          y[i] = s;
-        }
-      }
-      // neighbour blocks L^-, L^+ (rank <= 3, already scaled by M_d^-1)
-      const T* c = at.cpl[d] + (size_t)me[d] * (2 * NP + 8);
-      const long long estride = (d == 0) ? 1 : (d == 1 ? (long long)dm.ne[0] : (long long)dm.ne[0] * dm.ne[1]);
-      const int ned = dm.ne[d];
-      if (__ldg(c + 2 * NP + 2) != T(0)) {          // neighbour m-1 exists
-        long long en = (me[d] > 0) ? e - estride : e + (long long)(ned - 1) * estride;
-        const T* un = u + en * S::NODES + off;
-        T uP = T(0), dP = T(0);
-#pragma unroll
-        for (int a = 0; a < NP; ++a) {
-          T val = __ldg(un + a * stride);
-          dP = fma(__ldg(at.DP + a), val, dP);
-          if (a == P) uP = val;
-        }
-#pragma unroll
-        for (int i = 0; i < NP; ++i) y[i] = fma(__ldg(c + i), uP, y[i]);
-        y[0] += __ldg(c + 2 * NP + 0) * dP - __ldg(c + 2 * NP + 1) * uP;
-      }
-      if (__ldg(c + 2 * NP + 5) != T(0)) {          // neighbour m+1 exists
-        long long en = (me[d] < ned - 1) ? e + estride : e - (long long)(ned - 1) * estride;
-        const T* un = u + en * S::NODES + off;
-        T u0 = T(0), d0 = T(0);
-#pragma unroll
-        for (int a = 0; a < NP; ++a) {
-          T val = __ldg(un + a * stride);
-          d0 = fma(__ldg(at.D0 + a), val, d0);
-          if (a == 0) u0 = val;
-        }
-#pragma unroll
-        for (int i = 0; i < NP; ++i) y[i] = fma(__ldg(c + NP + i), u0, y[i]);
-        y[P] -= __ldg(c + 2 * NP + 3) * d0 + __ldg(c + 2 * NP + 4) * u0;
-      }
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        if (d == 0) ael[off + i * stride] = y[i];
-        else ael[off + i * stride] += y[i];
-      }
-    }
-    __syncthreads();
-  }
-  // v = (M_z (x) M_y (x) M_x) * (sum over axes of M_d^-1 L_d u)
-  for (int t = tid; t < nodes_blk; t += blockDim.x) {
-    long long g = e0 * S::NODES + t;
-    if (g >= total) continue;
-    const long long ee = g / S::NODES;
-    const int nd = (int)(g % S::NODES);
-    const int i = nd % NP, j = (nd / NP) % NP;
-    const int mx = (int)(ee % dm.ne[0]), my = (int)((ee / dm.ne[0]) % dm.ne[1]);
-    T m = __ldg(at.M[0] + (size_t)mx * NP + i) * __ldg(at.M[1] + (size_t)my * NP + j);
-    if (DIM == 3) {
-      const int k = nd / (NP * NP);
-      const int mz = (int)(ee / ((long long)dm.ne[0] * dm.ne[1]));
-      m *= __ldg(at.M[2] + (size_t)mz * NP + k);
-    }
-    const T val = m * acc[t];
-    v[g] = RESIDUAL ? f[g] - val : val;
-  }
-}
-
-template <typename T, int DIM, int NP>
-static int apply_dispatch(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f,
-                          T* v, cudaStream_t s) {
-  using S = ApplyShape<DIM, NP>;
-  long long blocks = (dm.nelem + S::EPB - 1) / S::EPB;
-  const size_t smem = 2 * sizeof(T) * S::EPB * S::NODES;
-  if (f) {
-    if (!set_smem(apply_kernel<T, DIM, NP, true>, smem)) return PMG_ECUDA;
-    count_launch(); apply_kernel<T, DIM, NP, true><<<(unsigned)blocks, S::THREADS, smem, s>>>(dm, at, u, f, v);
-  } else {
-    if (!set_smem(apply_kernel<T, DIM, NP, false>, smem)) return PMG_ECUDA;
-    count_launch(); apply_kernel<T, DIM, NP, false><<<(unsigned)blocks, S::THREADS, smem, s>>>(dm, at, u, f, v);
-  }
-  return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
-}
 
 template <typename T>
 int launch_apply(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f, T* v,
@@ -413,8 +227,47 @@ coarse_fdm_fused_kernel(LevelDims dm, CoarseFdm c, const double* f, double* u, d
   }
 }
 
+// The same passes as separate launches, for CUDA graphs whose branches run
+// concurrently (no grid-wide co-residency needed).
+__global__ void __launch_bounds__(256)
+coarse_pass_kernel(LevelDims dm, int axis, int transpose, const double* __restrict__ S, int N,
+                   const double* in, double* out) {
+  coarse_axis_pass(dm, axis, transpose != 0, S, N, in, out);
+}
+__global__ void __launch_bounds__(256)
+coarse_scale_kernel(LevelDims dm, CoarseFdm c, double* x, double tol) {
+  const int NX = dm.ne[0] * 2, NY = dm.ne[1] * 2, NZ = (dm.dim == 3) ? dm.ne[2] * 2 : 1;
+  const long long total = (long long)NX * NY * NZ;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int X = (int)(t % NX), Y = (int)((t / NX) % NY), Z = (int)(t / ((long long)NX * NY));
+    const double l = c.lam[0][X] + c.lam[1][Y] + (dm.dim == 3 ? c.lam[2][Z] : 0.0);
+    const long long o = coarse_off(dm, X, Y, Z);
+    x[o] = (l > tol) ? x[o] / l : 0.0;
+  }
+}
+
+static int launch_coarse_split(const LevelDims& dm, const CoarseFdm& c, const double* f, double* u,
+                               int blocks, double tol, cudaStream_t s) {
+  const double* src = f;
+  int cur = 0;
+  for (int d = 0; d < dm.dim; ++d) {
+    count_launch(); coarse_pass_kernel<<<blocks, 256, 0, s>>>(dm, d, 1, c.S[d], c.N[d], src, c.tmp[cur]);
+    src = c.tmp[cur];
+    cur ^= 1;
+  }
+  count_launch(); coarse_scale_kernel<<<blocks, 256, 0, s>>>(dm, c, c.tmp[cur ^ 1], tol);
+  for (int d = dm.dim - 1; d >= 0; --d) {
+    double* dst = (d == 0) ? u : c.tmp[cur];
+    count_launch(); coarse_pass_kernel<<<blocks, 256, 0, s>>>(dm, d, 0, c.S[d], c.N[d], src, dst);
+    src = dst;
+    cur ^= 1;
+  }
+  return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
+}
+
 int launch_coarse_fdm(const LevelDims& dm, const CoarseFdm& c, const double* f, double* u,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool cooperative) {
   static int per_sm = -1, nsm = 0;
   if (per_sm < 0) {
     int dev = 0;
@@ -428,9 +281,10 @@ int launch_coarse_fdm(const LevelDims& dm, const CoarseFdm& c, const double* f, 
   long long cap = (long long)per_sm * nsm;
   int blocks = (int)(want < cap ? want : cap);
   if (blocks < 1) blocks = 1;
+  double tol = 1e-13 * c.lam_max;
+  if (!cooperative) return launch_coarse_split(dm, c, f, u, blocks, tol, s);
   LevelDims dmv = dm;
   CoarseFdm cv = c;
-  double tol = 1e-13 * c.lam_max;
   const double* fv = f;
   double* uv = u;
   void* args[] = {&dmv, &cv, &fv, &uv, &tol};
@@ -537,7 +391,8 @@ __global__ void cg_update_kernel(double* __restrict__ u, double* __restrict__ r,
                                  double* __restrict__ r_old, const double* __restrict__ p,
                                  const double* __restrict__ q, const double* __restrict__ scal,
                                  int save_old, long long n, double* partial, unsigned* counter,
-                                 double* out_rr, int* status) {
+                                 double* out_rr, int* status, const int* it_dev) {
+  if (it_dev) save_old = *it_dev >= 2;
   const double pq = scal[S_PQ];
   const double alpha = scal[S_DELTA] / pq;
   if (blockIdx.x == 0 && threadIdx.x == 0 && status) {
@@ -560,26 +415,32 @@ __global__ void cg_update_kernel(double* __restrict__ u, double* __restrict__ r,
 
 void launch_cg_update(double* u, double* r, double* r_old, const double* p, const double* q,
                       const double* scal, int save_old, long long n, double* partial,
-                      unsigned* counter, double* out_rr, int* status, int nblocks, cudaStream_t s) {
+                      unsigned* counter, double* out_rr, int* status, int nblocks, cudaStream_t s,
+                      const int* it_dev) {
   count_launch(); cg_update_kernel<<<nblocks, 256, 0, s>>>(u, r, r_old, p, q, scal, save_old, n, partial, counter,
-                                           out_rr, status);
+                                           out_rr, status, it_dev);
 }
 
-// beta = (z.r - z.r_old) / delta_old ; p = z + beta p   (reading C8; first: r_old = 0)
+// beta = (z.r - z.r_old) / delta_old ; p = z + beta p   (reading C8; first: r_old = 0).
+// With it_dev (device-resident loop): iteration 1 sets the first direction p = z,
+// later iterations take z.r_old from the dot (r_old is zero until iteration 2
+// saves it, so the first beta is again Fletcher-Reeves).
 __global__ void p_update_kernel(double* __restrict__ p, const double* __restrict__ z,
-                                const double* __restrict__ scal, int first, long long n) {
+                                const double* __restrict__ scal, int first, long long n,
+                                const int* it_dev) {
+  const bool copy = it_dev && *it_dev == 1;
   const double zro = first ? 0.0 : scal[S_ZRO];
   const double beta = (scal[S_ZR] - zro) / scal[S_DELTA];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
-    p[t] = fma(beta, p[t], z[t]);
+    p[t] = copy ? z[t] : fma(beta, p[t], z[t]);
 }
 
 void launch_p_update(double* p, const double* z, const double* scal, int first, long long n,
-                     cudaStream_t s) {
+                     cudaStream_t s, const int* it_dev) {
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  count_launch(); p_update_kernel<<<(unsigned)blocks, 256, 0, s>>>(p, z, scal, first, n);
+  count_launch(); p_update_kernel<<<(unsigned)blocks, 256, 0, s>>>(p, z, scal, first, n, it_dev);
 }
 
 // delta <- z.r (after the p update, which still needed the old delta)
@@ -589,6 +450,58 @@ __global__ void set_delta_kernel(double* scal, int* status) {
 }
 void launch_set_delta(double* scal, int* status, cudaStream_t s) {
   count_launch(); set_delta_kernel<<<1, 1, 0, s>>>(scal, status);
+}
+
+// Device-resident MGCG control (Algorithm 2 with the convergence test on the
+// device).  ctrl[0] = status word of the vector kernels, ctrl[1] = current
+// iteration, ctrl[2] = result code.  The loop of a captured solve is a graph
+// `while` node whose condition these kernels set.
+__global__ void solve_begin_kernel(double* scal, int* ctrl, double* hist,
+                                   cudaGraphConditionalHandle cond) {
+  const double rr0 = scal[S_RR0];
+  const double r0 = sqrt(rr0);
+  hist[0] = r0;
+  scal[S_RR] = rr0;
+  const bool go = (r0 == r0) && r0 != 0.0;
+  ctrl[1] = go ? 1 : 0;
+  ctrl[2] = (r0 == r0) ? (go ? PMG_ENOCONV : PMG_OK) : PMG_ENAN;
+  cudaGraphSetConditional(cond, go ? 1u : 0u);
+}
+
+// After iteration ctrl[1]: record ||r||, stop on a device status, on
+// ||r|| <= rtol ||r_0|| or at max_iter; else advance the iteration counter.
+__global__ void solve_control_kernel(const double* scal, int* ctrl, double* hist, double rtol,
+                                     int max_iter, cudaGraphConditionalHandle cond) {
+  const int it = ctrl[1];
+  const double rn = sqrt(scal[S_RR]);
+  const double r0 = sqrt(scal[S_RR0]);
+  hist[it] = rn;
+  unsigned go = 0;
+  if (ctrl[0] != 0) ctrl[2] = ctrl[0];
+  else if (rn <= rtol * r0) ctrl[2] = PMG_OK;
+  else if (it >= max_iter) ctrl[2] = PMG_ENOCONV;
+  else { go = 1; ctrl[1] = it + 1; }
+  cudaGraphSetConditional(cond, go);
+}
+
+__global__ void solve_result_kernel(const double* scal, const int* ctrl, SolveResult* out) {
+  out->r0 = sqrt(scal[S_RR0]);
+  out->rn = sqrt(scal[S_RR]);
+  out->iterations = ctrl[1];
+  out->status = ctrl[2];
+}
+
+void launch_solve_result(const double* scal, const int* ctrl, SolveResult* out, cudaStream_t s) {
+  count_launch(); solve_result_kernel<<<1, 1, 0, s>>>(scal, ctrl, out);
+}
+
+void launch_solve_begin(double* scal, int* ctrl, double* hist, cudaGraphConditionalHandle cond,
+                        cudaStream_t s) {
+  count_launch(); solve_begin_kernel<<<1, 1, 0, s>>>(scal, ctrl, hist, cond);
+}
+void launch_solve_control(const double* scal, int* ctrl, double* hist, double rtol, int max_iter,
+                          cudaGraphConditionalHandle cond, cudaStream_t s) {
+  count_launch(); solve_control_kernel<<<1, 1, 0, s>>>(scal, ctrl, hist, rtol, max_iter, cond);
 }
 
 // x -= mean(x)   (projection onto range(A) for periodic grids)

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/pmg.h"
+#include "dfloat.cuh"
 
 namespace pmg {
 
@@ -81,10 +82,16 @@ struct FdmAxis {
   const int* sym; // [count] 1: centro-symmetric, tables stored in even-odd folded form
 };
 
+// Largest CTA any patch-kernel launch may use (the autotuner's candidates stay
+// within it; it caps registers at 128 per thread).
+constexpr int kFdmMaxThreads = 512;
+
 template <typename T>
 struct FdmFamily {
   FdmAxis<T> ax[3];    // patch-buffer axes a (fastest), b, c
   int count_total;
+  int tc = 0;          // fp32 only: 1 = line passes on the tensor cores (tables unfolded)
+  int threads = 0;     // CTA size chosen by the autotuner (0: the kernel's default)
 };
 
 struct LevelDims {
@@ -129,6 +136,12 @@ struct Grid {
   double beta[3] = {0, 0, 0};
 };
 
+// Result of one device-resident solve, written by the device.
+struct SolveResult {
+  double r0, rn;
+  int iterations, status;
+};
+
 struct Hier {
   Grid grid;
   pmg_options opt{};
@@ -164,6 +177,20 @@ struct Hier {
   int pc_state = 0;
   int pc_calls = 0;
   unsigned long long pc_launches = 0;
+  // Whole MGCG solve as one CUDA graph (a device-side `while` node runs the
+  // iterations), captured for fixed (g, u, rtol) once the kernels have run
+  // directly; state 0 = not yet, 1 = captured, -1 = conditional graphs unsupported
+  cudaStream_t cap_stream2 = nullptr;
+  cudaGraphExec_t sv_exec = nullptr;
+  int sv_state = 0;
+  const double* sv_g = nullptr;
+  double* sv_u = nullptr;
+  double sv_rtol = -1.0;
+  unsigned long long sv_fixed = 0, sv_iter = 0;   // kernels outside / per iteration
+  double* hist = nullptr;          // device residual history [max_iter + 1]
+  SolveResult* dres = nullptr;     // device result of the captured solve
+  bool coarse_split = false;       // coarse solve as separate launches (graph capture)
+  ApplyTables<dfloat> at_df{};     // finest-level apply tables in double-float (outer_apply DF)
 };
 
 // scalar slots
@@ -183,6 +210,7 @@ int overlap_nodes(int P_l, int policy);
 double transition(double x, int weighting);
 void ec_axis_tables(const Axis1DHost& a, int No, int weighting, double tau, AxisTables& t);
 void fc_axis_tables(const Axis1DHost& a, int weighting, double tau, AxisTables& t);
+void unfold_tables(AxisTables& t);
 void global_axis_eig(const Axis1DHost& a, std::vector<double>& S, std::vector<double>& lam);
 
 // ----------------------------------------------------------------------------
@@ -199,18 +227,26 @@ int launch_restrict(const LevelDims& fine, const LevelDims& coarse, const T* J, 
 template <typename T>
 int launch_prolong(const LevelDims& fine, const LevelDims& coarse, const T* J, const T* uc, T* uf,
                    cudaStream_t s);
+int launch_apply_df(const LevelDims& dm, const ApplyTables<dfloat>& at, const double* u,
+                    const double* f, double* v, cudaStream_t s);
 int launch_coarse_fdm(const LevelDims& dm, const CoarseFdm& c, const double* f, double* u,
-                      cudaStream_t s);
+                      cudaStream_t s, bool cooperative = true);
 template <typename Ta, typename Tb>
 void launch_convert(const Ta* in, Tb* out, long long n, cudaStream_t s);
 void launch_dot(const double* x, const double* y, const double* y2, long long n, double* partial,
                 unsigned* counter, double* out, int nblocks, cudaStream_t s);
 void launch_cg_update(double* u, double* r, double* r_old, const double* p, const double* q,
                       const double* scal, int save_old, long long n, double* partial,
-                      unsigned* counter, double* out_rr, int* status, int nblocks, cudaStream_t s);
+                      unsigned* counter, double* out_rr, int* status, int nblocks, cudaStream_t s,
+                      const int* it_dev = nullptr);
 void launch_p_update(double* p, const double* z, const double* scal, int first, long long n,
-                     cudaStream_t s);
+                     cudaStream_t s, const int* it_dev = nullptr);
 void launch_set_delta(double* scal, int* status, cudaStream_t s);
+void launch_solve_begin(double* scal, int* ctrl, double* hist, cudaGraphConditionalHandle cond,
+                        cudaStream_t s);
+void launch_solve_control(const double* scal, int* ctrl, double* hist, double rtol, int max_iter,
+                          cudaGraphConditionalHandle cond, cudaStream_t s);
+void launch_solve_result(const double* scal, const int* ctrl, SolveResult* out, cudaStream_t s);
 void launch_sub_mean(double* x, long long n, double* partial, unsigned* counter, double* scal,
                      int nblocks, cudaStream_t s);
 void launch_mass(const LevelDims& dm, const ApplyTables<double>& at, const double* f, double* g,

@@ -582,4 +582,40 @@ void apply_axis_tables(const Axis1DHost& a, ApplyAxisHost& t) {
   }
 }
 
+// Expand even-odd folded patch tables (sym = 1) into the general layout
+// (S node-major, W^T mode-major, symmetric modes first), for the tensor-core
+// line passes, which apply the full n x n tables.
+void unfold_tables(AxisTables& t) {
+  const int n = t.n, H = n / 2, NE = n - H, NO = H;
+  std::vector<double> Sf((size_t)n * n), Wf((size_t)n * n);
+  for (int p = 0; p < t.count; ++p) {
+    if (!t.sym[p]) continue;
+    const double* S = &t.S[(size_t)p * n * n];
+    const double* W = &t.W[(size_t)p * n * n];
+    std::fill(Sf.begin(), Sf.end(), 0.0);
+    std::fill(Wf.begin(), Wf.end(), 0.0);
+    for (int i = 0; i < NE; ++i)
+      for (int a = 0; a < NE; ++a) {
+        const double s = S[(size_t)a * NE + i], w = W[(size_t)i * NE + a];
+        Sf[(size_t)a * n + i] = s;
+        Sf[(size_t)(n - 1 - a) * n + i] = s;
+        Wf[(size_t)i * n + a] = w;
+        Wf[(size_t)i * n + (n - 1 - a)] = w;
+      }
+    const double* So = S + (size_t)NE * NE;
+    const double* Wo = W + (size_t)NE * NE;
+    for (int i = 0; i < NO; ++i)
+      for (int a = 0; a < NO; ++a) {
+        const double s = So[(size_t)a * NO + i], w = Wo[(size_t)i * NO + a];
+        Sf[(size_t)a * n + NE + i] = s;
+        Sf[(size_t)(n - 1 - a) * n + NE + i] = -s;
+        Wf[(size_t)(NE + i) * n + a] = w;
+        Wf[(size_t)(NE + i) * n + (n - 1 - a)] = -w;
+      }
+    std::copy(Sf.begin(), Sf.end(), t.S.begin() + (size_t)p * n * n);
+    std::copy(Wf.begin(), Wf.end(), t.W.begin() + (size_t)p * n * n);
+    t.sym[p] = 0;
+  }
+}
+
 }  // namespace pmg

@@ -4,12 +4,16 @@
 // Every per-iteration step is a kernel launched on the caller's stream; the
 // host only sequences launches and, once per CG iteration, reads the residual
 // norm to test convergence.
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <exception>
+#include <map>
+#include <mutex>
 #include <new>
 
+#include "dfloat.cuh"
 #include "pmg_internal.h"
 
 namespace pmg {
@@ -121,39 +125,59 @@ FdmAxis<T> upload_axis(std::vector<void*>& owned, const AxisTables& t, const Axi
   return ax;
 }
 
+// operator-apply tables of level l in arithmetic T
 template <typename T>
-void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTables>& ec,
-                     const std::vector<AxisTables>& fc) {
+ApplyTables<T> build_apply_tables(Hier& h, int l, std::vector<void*>& own) {
   const LevelDims& dm = h.dims[l];
   auto& ax = h.axes[l];
-  auto& own = dev.owned;
+  ApplyTables<T> at{};
   for (int d = 0; d < 3; ++d) {
     int dd = d < dm.dim ? d : 0;
     ApplyAxisHost t;
     apply_axis_tables(ax[dd], t);
-    dev.at.L0[d] = dev_upload<T>(own, t.L0);
-    dev.at.sym[d] = dev_upload_int(own, t.sym);
-    dev.at.M[d] = dev_upload<T>(own, ax[dd].M);
-    dev.at.cpl[d] = dev_upload<T>(own, t.cpl);
+    at.L0[d] = dev_upload<T>(own, t.L0);
+    at.sym[d] = dev_upload_int(own, t.sym);
+    at.M[d] = dev_upload<T>(own, ax[dd].M);
+    at.cpl[d] = dev_upload<T>(own, t.cpl);
   }
   std::vector<double> D0(dm.NP), DP(dm.NP);
   for (int k = 0; k < dm.NP; ++k) {
     D0[k] = ax[0].D[0 * dm.NP + k];
     DP[k] = ax[0].D[(size_t)(dm.NP - 1) * dm.NP + k];
   }
-  dev.at.D0 = dev_upload<T>(own, D0);
-  dev.at.DP = dev_upload<T>(own, DP);
+  at.D0 = dev_upload<T>(own, D0);
+  at.DP = dev_upload<T>(own, DP);
+  return at;
+}
+
+template <typename T>
+void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTables>& ec,
+                     const std::vector<AxisTables>& fc) {
+  const LevelDims& dm = h.dims[l];
+  auto& ax = h.axes[l];
+  auto& own = dev.owned;
+  dev.at = build_apply_tables<T>(h, l, own);
   dev.u = dev_alloc<T>(own, dm.ndof);
   dev.f = dev_alloc<T>(own, dm.ndof);
   dev.r = dev_alloc<T>(own, dm.ndof);
   if (l == 0) return;
+  // tensor-core line passes (fp32, 3-D) apply the full tables: unfold even-odd ones
+  const int tc = (sizeof(T) == 4 && h.opt.precision == PMG_PREC_MIXED_TC && dm.dim == 3) ? 1 : 0;
+  std::vector<AxisTables> ecu, fcu;
+  const std::vector<AxisTables>& E = tc ? (ecu = ec) : ec;
+  const std::vector<AxisTables>& F = tc ? (fcu = fc) : fc;
+  if (tc) {
+    for (auto& t : ecu) unfold_tables(t);
+    for (auto& t : fcu) unfold_tables(t);
+  }
   if (h.opt.smoother == PMG_SMOOTHER_EA) {
     FdmFamily<T> fam{};
     fam.count_total = 1;
+    fam.tc = tc;
     for (int q = 0; q < 3; ++q) {
       if (q < dm.dim) {
-        fam.ax[q] = upload_axis<T>(own, ec[q], ax[q], q, q == 0 ? level_omega(h.opt, l) : 1.0);
-        fam.count_total *= ec[q].count;
+        fam.ax[q] = upload_axis<T>(own, E[q], ax[q], q, q == 0 ? level_omega(h.opt, l) : 1.0);
+        fam.count_total *= E[q].count;
       } else {
         fam.ax[q] = trivial_axis<T>(own);
       }
@@ -162,13 +186,14 @@ void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTab
   } else {
     for (int nrm = 0; nrm < dm.dim; ++nrm) {
       FdmFamily<T> fam{};
-      fam.ax[0] = upload_axis<T>(own, fc[nrm], ax[nrm], nrm, level_omega(h.opt, l));
-      fam.count_total = fc[nrm].count;
+      fam.tc = tc;
+      fam.ax[0] = upload_axis<T>(own, F[nrm], ax[nrm], nrm, level_omega(h.opt, l));
+      fam.count_total = F[nrm].count;
       int q = 1;
       for (int d = 0; d < dm.dim; ++d) {
         if (d == nrm) continue;
-        fam.ax[q] = upload_axis<T>(own, ec[d], ax[d], d, 1.0);
-        fam.count_total *= ec[d].count;
+        fam.ax[q] = upload_axis<T>(own, E[d], ax[d], d, 1.0);
+        fam.count_total *= E[d].count;
         ++q;
       }
       for (; q < 3; ++q) fam.ax[q] = trivial_axis<T>(own);
@@ -249,10 +274,10 @@ void vcycle(Hier& h, const T* fL, T* uL, cudaStream_t s) {
   }
   // coarse grid solution in fp64 (Algorithm 1, A_0^+ f_0)
   if constexpr (sizeof(T) == 8) {
-    PMG_CHECK(launch_coarse_fdm(h.dims[0], h.coarse, h.d64[0].f, h.d64[0].u, s));
+    PMG_CHECK(launch_coarse_fdm(h.dims[0], h.coarse, h.d64[0].f, h.d64[0].u, s, !h.coarse_split));
   } else {
     launch_convert<float, double>(h.d32[0].f, h.d64[0].f, h.dims[0].ndof, s);
-    PMG_CHECK(launch_coarse_fdm(h.dims[0], h.coarse, h.d64[0].f, h.d64[0].u, s));
+    PMG_CHECK(launch_coarse_fdm(h.dims[0], h.coarse, h.d64[0].f, h.d64[0].u, s, !h.coarse_split));
     launch_convert<double, float>(h.d64[0].u, h.d32[0].u, h.dims[0].ndof, s);
   }
   for (int l = 1; l <= L; ++l) {
@@ -265,7 +290,11 @@ void vcycle(Hier& h, const T* fL, T* uL, cudaStream_t s) {
 
 // z = V-cycle(r) in the hierarchy's precision, fp64 in and out.
 void precondition(Hier& h, const double* r, double* z, cudaStream_t s) {
-  if (h.opt.precision == PMG_PREC_MIXED) {
+  if (h.opt.preconditioner == PMG_PC_NONE) {         // plain CG: z = r
+    PMG_CUDA(cudaMemcpyAsync(z, r, sizeof(double) * h.dims[h.L].ndof, cudaMemcpyDeviceToDevice, s));
+    return;
+  }
+  if (h.opt.precision != PMG_PREC_FP64) {
     const long long n = h.dims[h.L].ndof;
     launch_convert<double, float>(r, h.d32[h.L].f, n, s);
     vcycle<float>(h, h.d32[h.L].f, h.d32[h.L].u, s);
@@ -312,6 +341,150 @@ void precondition_graph(Hier& h, cudaStream_t s) {
   if (h.pc_state == 0) h.pc_launches = g_launches.load() - c0;
 }
 
+// The outer CG's operator apply on the finest level: v = A u, or v = f - A u
+// (f non-null); FP64, or double-float on the FP32 pipes (outer_apply option).
+void outer_apply(Hier& h, const double* u, const double* f, double* v, cudaStream_t s) {
+  const LevelDims& dm = h.dims[h.L];
+  if (h.opt.outer_apply == PMG_OUTER_DF) {
+    PMG_CHECK(launch_apply_df(dm, h.at_df, u, f, v, s));
+  } else {
+    PMG_CHECK(launch_apply<double>(dm, h.d64[h.L].at, u, f, v, s));
+  }
+}
+
+// Appends one whole MGCG solve of h on (g, u) to `graph` as an independent
+// branch (Algorithm 2): r = g - A u and ||r_0||, then the iterations as a
+// device-side `while` node whose body is z = V-cycle(r), beta and p, q = A p,
+// alpha, the u and r updates and the test ||r|| <= rtol ||r_0||; finally the
+// solve's result is written to *res.  The coarse solve is captured as separate
+// launches, so branches of one graph may run concurrently.  Returns the kernel
+// counts outside the loop and per iteration.
+void capture_solve(Hier& h, cudaGraph_t graph, const double* g, double* u, double rtol,
+                   SolveResult* res, unsigned long long* fixed, unsigned long long* per_iter) {
+  const int L = h.L;
+  const LevelDims& dm = h.dims[L];
+  const long long n = dm.ndof;
+  const int nb = reduce_blocks(n);
+  if (!h.cap_stream) PMG_CUDA(cudaStreamCreateWithFlags(&h.cap_stream, cudaStreamNonBlocking));
+  if (!h.cap_stream2) PMG_CUDA(cudaStreamCreateWithFlags(&h.cap_stream2, cudaStreamNonBlocking));
+  cudaStream_t cs = h.cap_stream, cb = h.cap_stream2;
+  cudaGraphConditionalHandle cond;
+  PMG_CUDA(cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault));
+  const unsigned long long c0 = g_launches.load();
+  unsigned long long c1 = 0, c2 = 0;
+  h.coarse_split = true;
+  bool outer = false, inner = false;
+  try {
+    PMG_CUDA(cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed));
+    outer = true;
+    PMG_CUDA(cudaMemsetAsync(h.dstatus, 0, 4 * sizeof(int), cs));
+    outer_apply(h, u, g, h.r, cs);
+    if (dm.periodic) launch_sub_mean(h.r, n, h.partial, h.counter, h.scal, nb, cs);
+    launch_dot(h.r, h.r, nullptr, n, h.partial, h.counter, h.scal + S_RR0, nb, cs);
+    PMG_CUDA(cudaMemsetAsync(h.r_old, 0, n * sizeof(double), cs));
+    launch_solve_begin(h.scal, h.dstatus, h.hist, cond, cs);
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t ndeps = 0;
+    PMG_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, &edges, &ndeps));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop = nullptr;
+    PMG_CUDA(cudaGraphAddNode(&loop, graph, deps, edges, ndeps, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    c1 = g_launches.load();
+    PMG_CUDA(cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed));
+    inner = true;
+    precondition(h, h.r, h.z, cb);
+    launch_dot(h.z, h.r, h.r_old, n, h.partial, h.counter, h.scal + S_ZR, nb, cb);
+    launch_p_update(h.p, h.z, h.scal, 0, n, cb, h.dstatus + 1);
+    launch_set_delta(h.scal, h.dstatus, cb);
+    outer_apply(h, h.p, nullptr, h.q, cb);
+    launch_dot(h.p, h.q, nullptr, n, h.partial, h.counter, h.scal + S_PQ, nb, cb);
+    launch_cg_update(u, h.r, h.r_old, h.p, h.q, h.scal, 0, n, h.partial, h.counter, h.scal + S_RR,
+                     h.dstatus, nb, cb, h.dstatus + 1);
+    launch_solve_control(h.scal, h.dstatus, h.hist, rtol, h.opt.max_iter, cond, cb);
+    cudaGraph_t body_out = nullptr;
+    inner = false;
+    PMG_CUDA(cudaStreamEndCapture(cb, &body_out));
+    c2 = g_launches.load();
+    PMG_CUDA(cudaStreamUpdateCaptureDependencies(cs, &loop, nullptr, 1,
+                                                 cudaStreamSetCaptureDependencies));
+    if (dm.periodic) launch_sub_mean(u, n, h.partial, h.counter, h.scal, nb, cs);
+    launch_solve_result(h.scal, h.dstatus, res, cs);
+    cudaGraph_t out = nullptr;
+    outer = false;
+    PMG_CUDA(cudaStreamEndCapture(cs, &out));
+  } catch (...) {
+    cudaGraph_t tmp = nullptr;
+    if (inner) cudaStreamEndCapture(cb, &tmp);
+    if (outer) cudaStreamEndCapture(cs, &tmp);
+    cudaGetLastError();
+    h.coarse_split = false;
+    g_launches.store(c0);
+    throw;
+  }
+  h.coarse_split = false;
+  *per_iter = c2 - c1;
+  *fixed = (g_launches.load() - c0) - *per_iter;
+  g_launches.store(c0);                     // captured launches did not run
+}
+
+// Capture (or re-capture for new g, u, rtol) the single-solve graph of h.
+void build_solve_graph(Hier& h, const double* g, double* u, double rtol) {
+  if (h.sv_exec) cudaGraphExecDestroy(h.sv_exec);
+  h.sv_exec = nullptr;
+  h.sv_state = 0;
+  cudaGraph_t graph = nullptr;
+  try {
+    PMG_CUDA(cudaGraphCreate(&graph, 0));
+    capture_solve(h, graph, g, u, rtol, h.dres, &h.sv_fixed, &h.sv_iter);
+    PMG_CUDA(cudaGraphInstantiate(&h.sv_exec, graph, 0));
+    h.sv_state = 1;
+    h.sv_g = g;
+    h.sv_u = u;
+    h.sv_rtol = rtol;
+  } catch (const CudaError& e) {
+    h.err = "device-resident solve unavailable, host-driven iterations used: " + e.msg;
+    h.sv_exec = nullptr;
+    h.sv_state = -1;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+}
+
+void fill_stats(pmg_stats* st, const SolveResult& r, const double* hist, cudaStream_t s) {
+  if (!st) return;
+  st->iterations = r.iterations;
+  st->r0 = r.r0;
+  st->rn = r.rn;
+  st->status = r.status;
+  st->device_loop = 1;
+  if (st->history) {
+    PMG_CUDA(cudaMemcpyAsync(st->history, hist, sizeof(double) * (r.iterations + 1),
+                             cudaMemcpyDeviceToHost, s));
+    PMG_CUDA(cudaStreamSynchronize(s));
+  }
+}
+
+int solve_graph_run(Hier& h, pmg_stats* st, cudaStream_t s) {
+  PMG_CUDA(cudaGraphLaunch(h.sv_exec, s));
+  PMG_CUDA(cudaMemcpyAsync(h.hscal, h.dres, sizeof(SolveResult), cudaMemcpyDeviceToHost, s));
+  PMG_CUDA(cudaStreamSynchronize(s));
+  SolveResult r;
+  std::memcpy(&r, h.hscal, sizeof r);
+  g_launches.fetch_add(h.sv_fixed + (unsigned long long)r.iterations * h.sv_iter,
+                       std::memory_order_relaxed);
+  fill_stats(st, r, h.hist, s);
+  return r.status;
+}
+
 void read_scalars(Hier& h, cudaStream_t s, int* status) {
   PMG_CUDA(cudaMemcpyAsync(h.hscal, h.scal, sizeof(double) * S_NUM, cudaMemcpyDeviceToHost, s));
   PMG_CUDA(cudaMemcpyAsync(h.hscal + S_NUM, h.dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -319,14 +492,104 @@ void read_scalars(Hier& h, cudaStream_t s, int* status) {
   std::memcpy(status, h.hscal + S_NUM, sizeof(int));
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner of the patch kernel's CTA size.  Every line pass strides over its
+// lines by the CTA size, so any multiple of 32 up to kFdmMaxThreads computes
+// the same result; the best size depends on the patch shape (shared memory
+// per CTA, lines per pass) and on the number of patches.  Each family is timed
+// on its own level with CUDA events; results are cached per shape for the
+// process, so many hierarchies of one shape tune once.
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::array<int, 6>, int> g_tune_cache;
+
+template <typename T>
+int tune_family(Hier& h, int l, FdmFamily<T>& fam, LevelDev<T>& d, cudaStream_t s) {
+  int lg = 0;
+  while ((1 << (lg + 1)) <= fam.count_total) ++lg;
+  const std::array<int, 6> key = {(int)sizeof(T), fam.ax[0].n, fam.ax[1].n, fam.ax[2].n, fam.tc, lg};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) return fam.threads = it->second;
+  }
+  const LevelDims& dm = h.dims[l];
+  PMG_CUDA(cudaMemsetAsync(d.f, 0, sizeof(T) * dm.ndof, s));
+  PMG_CUDA(cudaMemsetAsync(d.u, 0, sizeof(T) * dm.ndof, s));
+  static const int cand[] = {64, 96, 128, 160, 192, 256, 320, 384, 448, 512};
+  cudaEvent_t e0, e1;
+  PMG_CUDA(cudaEventCreate(&e0));
+  PMG_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 1e30f;
+  try {
+    for (int c : cand) {
+      if (c > kFdmMaxThreads) continue;
+      fam.threads = c;
+      PMG_CHECK(launch_fdm<T>(dm, fam, d.f, d.u, s));            // warm-up
+      PMG_CUDA(cudaEventRecord(e0, s));
+      for (int rep = 0; rep < 3; ++rep) PMG_CHECK(launch_fdm<T>(dm, fam, d.f, d.u, s));
+      PMG_CUDA(cudaEventRecord(e1, s));
+      PMG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      PMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    fam.threads = 0;
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  fam.threads = best;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[key] = best;
+  return best;
+}
+
+template <typename T>
+void tune_level(Hier& h, int l, LevelDev<T>& d, cudaStream_t s) {
+  if (h.opt.smoother == PMG_SMOOTHER_EA) {
+    tune_family<T>(h, l, d.ea, d, s);
+  } else {
+    for (int q = 0; q < h.dims[l].dim; ++q) tune_family<T>(h, l, d.fa[q], d, s);
+  }
+}
+
+// Algorithm 2.  The first solve of a hierarchy runs its iterations from the
+// host (one synchronisation per iteration; it also sets the kernels up); later
+// solves replay the whole solve as one CUDA graph with a device-side loop.
+int solve_host_loop(Hier& h, const double* g, double* u, double rtol, pmg_stats* st,
+                    cudaStream_t s);
+
 int solve_impl(Hier& h, const double* g, double* u, double rtol, pmg_stats* st, cudaStream_t s) {
+  if (h.pc_calls >= 1 && h.sv_state >= 0) {
+    if (h.sv_state == 0 || h.sv_g != g || h.sv_u != u || h.sv_rtol != rtol)
+      build_solve_graph(h, g, u, rtol);
+    if (h.sv_state == 1) return solve_graph_run(h, st, s);
+  }
+  const int rc = solve_host_loop(h, g, u, rtol, st, s);
+  if (st) {
+    st->status = rc;
+    st->device_loop = 0;
+  }
+  return rc;
+}
+
+int solve_host_loop(Hier& h, const double* g, double* u, double rtol, pmg_stats* st,
+                    cudaStream_t s) {
   const int L = h.L;
   const LevelDims& dm = h.dims[L];
   const long long n = dm.ndof;
   const int nb = reduce_blocks(n);
   PMG_CUDA(cudaMemsetAsync(h.dstatus, 0, sizeof(int), s));
   // r = g - A u (fp64); periodic: project onto range(A)
-  PMG_CHECK(launch_apply<double>(dm, h.d64[L].at, u, g, h.r, s));
+  outer_apply(h, u, g, h.r, s);
   if (dm.periodic) launch_sub_mean(h.r, n, h.partial, h.counter, h.scal, nb, s);
   launch_dot(h.r, h.r, nullptr, n, h.partial, h.counter, h.scal + S_RR0, nb, s);
   int status = 0;
@@ -339,13 +602,16 @@ int solve_impl(Hier& h, const double* g, double* u, double rtol, pmg_stats* st, 
     if (st->history) st->history[0] = r0;
   }
   if (!(r0 == r0)) return PMG_ENAN;
-  if (r0 == 0.0) return PMG_OK;
+  if (r0 == 0.0) {
+    if (dm.periodic) launch_sub_mean(u, n, h.partial, h.counter, h.scal, nb, s);
+    return PMG_OK;
+  }
   precondition_graph(h, s);
   PMG_CUDA(cudaMemcpyAsync(h.p, h.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   launch_dot(h.p, h.r, nullptr, n, h.partial, h.counter, h.scal + S_DELTA, nb, s);
   int rc = PMG_ENOCONV;
   for (int it = 1; it <= h.opt.max_iter; ++it) {
-    PMG_CHECK(launch_apply<double>(dm, h.d64[L].at, h.p, nullptr, h.q, s));
+    outer_apply(h, h.p, nullptr, h.q, s);
     launch_dot(h.p, h.q, nullptr, n, h.partial, h.counter, h.scal + S_PQ, nb, s);
     launch_cg_update(u, h.r, h.r_old, h.p, h.q, h.scal, it >= 2 ? 1 : 0, n, h.partial, h.counter,
                      h.scal + S_RR, h.dstatus, nb, s);
@@ -366,6 +632,28 @@ int solve_impl(Hier& h, const double* g, double* u, double rtol, pmg_stats* st, 
   if (dm.periodic) launch_sub_mean(u, n, h.partial, h.counter, h.scal, nb, s);
   PMG_CUDA(cudaGetLastError());
   return rc;
+}
+
+// A batch of independent solves captured as one CUDA graph: one branch per
+// (hierarchy, g, u), each with its own device-side iteration loop.
+struct Batch {
+  std::vector<Hier*> h;
+  std::vector<const double*> g;
+  std::vector<double*> u;
+  double rtol = 0.0;
+  cudaGraphExec_t exec = nullptr;
+  SolveResult* dres = nullptr;     // device [count]
+  SolveResult* hres = nullptr;     // pinned host [count]
+  std::vector<unsigned long long> fixed, per_iter;
+  std::vector<void*> owned;
+  std::string err;
+};
+
+void free_batch(Batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (void* p : b->owned) cudaFree(p);
+  if (b->hres) cudaFreeHost(b->hres);
+  delete b;
 }
 
 Hier* H(pmg_hier h) { return reinterpret_cast<Hier*>(h); }
@@ -395,7 +683,9 @@ void free_all(Hier* h) {
   for (void* p : h->owned) cudaFree(p);
   if (h->hscal) cudaFreeHost(h->hscal);
   if (h->pc_exec) cudaGraphExecDestroy(h->pc_exec);
+  if (h->sv_exec) cudaGraphExecDestroy(h->sv_exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
 }
 
 }  // namespace
@@ -417,6 +707,8 @@ void pmg_options_default(pmg_options* opt) {
   opt->precision = PMG_PREC_FP64;
   opt->max_iter = 100;
   for (int l = 0; l < 8; ++l) opt->omega_level[l] = opt->tau_level[l] = 0.0;
+  opt->preconditioner = PMG_PC_VCYCLE;
+  opt->outer_apply = PMG_OUTER_FP64;
 }
 
 int pmg_grid_create(int dim, int P, const int n_elem[3], const double* const spacing[3],
@@ -476,7 +768,10 @@ int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
   if (o.ns_pre < 0 || o.ns_post < 0 || o.max_iter < 1 || !(o.omega > 0.0)) return PMG_EINVAL;
   for (int l = 0; l < 8; ++l)
     if (!(o.omega_level[l] >= 0.0) || !(o.tau_level[l] >= 0.0) || o.tau_level[l] > 1.0) return PMG_EINVAL;
-  if (o.precision != PMG_PREC_FP64 && o.precision != PMG_PREC_MIXED) return PMG_EINVAL;
+  if (o.precision != PMG_PREC_FP64 && o.precision != PMG_PREC_MIXED && o.precision != PMG_PREC_MIXED_TC)
+    return PMG_EINVAL;
+  if (o.preconditioner != PMG_PC_VCYCLE && o.preconditioner != PMG_PC_NONE) return PMG_EINVAL;
+  if (o.outer_apply != PMG_OUTER_FP64 && o.outer_apply != PMG_OUTER_DF) return PMG_EINVAL;
   Hier* h = nullptr;
   try {
     h = new Hier();
@@ -521,7 +816,7 @@ int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
         }
       }
       build_level_dev<double>(*h, l, h->d64[l], ec, fc);
-      if (o.precision == PMG_PREC_MIXED) build_level_dev<float>(*h, l, h->d32[l], ec, fc);
+      if (o.precision != PMG_PREC_FP64) build_level_dev<float>(*h, l, h->d32[l], ec, fc);
       for (auto& t : ec) { t.S.clear(); t.W.clear(); t.lam.clear(); }
       for (auto& t : fc) { t.S.clear(); t.W.clear(); t.lam.clear(); }
       h->ec_shape[l] = ec;
@@ -533,7 +828,8 @@ int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
         h->J32[l] = dev_upload<float>(h->owned, J);
       }
     }
-    h->has32 = o.precision == PMG_PREC_MIXED;
+    h->has32 = o.precision != PMG_PREC_FP64;
+    if (o.outer_apply == PMG_OUTER_DF) h->at_df = build_apply_tables<dfloat>(*h, L, h->owned);
     // exact coarse solve tables (global 1-D eigen-pairs at P = 1)
     CoarseFdm& c = h->coarse;
     c.lam_max = 0.0;
@@ -558,6 +854,8 @@ int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
     h->partial = dev_alloc<double>(h->owned, 2 * 152 * 8 + 64);
     h->counter = dev_alloc<unsigned>(h->owned, 4);
     h->dstatus = dev_alloc<int>(h->owned, 4);
+    h->hist = dev_alloc<double>(h->owned, (size_t)o.max_iter + 1);
+    h->dres = dev_alloc<SolveResult>(h->owned, 1);
     PMG_CUDA(cudaMemset(h->counter, 0, 4 * sizeof(unsigned)));
     PMG_CUDA(cudaMemset(h->dstatus, 0, 4 * sizeof(int)));
     PMG_CUDA(cudaMemset(h->scal, 0, S_NUM * sizeof(double)));
@@ -597,6 +895,10 @@ int pmg_apply(pmg_hier hh, int level, const double* u, double* Au, void* stream)
   Hier* h = H(hh);
   if (!h || level < 0 || level > h->L || !u || !Au) return PMG_EINVAL;
   return guarded(h, [&] {
+    if (level == h->L) {
+      outer_apply(*h, u, nullptr, Au, (cudaStream_t)stream);
+      return (int)PMG_OK;
+    }
     return launch_apply<double>(h->dims[level], h->d64[level].at, u, nullptr, Au, (cudaStream_t)stream);
   });
 }
@@ -605,6 +907,10 @@ int pmg_residual(pmg_hier hh, int level, const double* u, const double* f, doubl
   Hier* h = H(hh);
   if (!h || level < 0 || level > h->L || !u || !f || !r) return PMG_EINVAL;
   return guarded(h, [&] {
+    if (level == h->L) {
+      outer_apply(*h, u, f, r, (cudaStream_t)stream);
+      return (int)PMG_OK;
+    }
     return launch_apply<double>(h->dims[level], h->d64[level].at, u, f, r, (cudaStream_t)stream);
   });
 }
@@ -624,7 +930,7 @@ int pmg_smooth(pmg_hier hh, int level, double* u, const double* f, int nsteps, v
   if (!h || level < 1 || level > h->L || !u || !f || nsteps < 0) return PMG_EINVAL;
   return guarded(h, [&] {
     cudaStream_t s = (cudaStream_t)stream;
-    if (h->opt.precision == PMG_PREC_MIXED) {
+    if (h->opt.precision != PMG_PREC_FP64) {
       const long long n = h->dims[level].ndof;
       // level vectors of the V-cycle serve as fp32 staging buffers
       float* uf = h->d32[level].u;
@@ -701,6 +1007,133 @@ int pmg_solve_host(pmg_hier hh, const double* g_host, double* u_host, double rto
   });
 }
 
+int pmg_batch_create(int count, const pmg_hier* hiers, const double* const* g_dev,
+                     double* const* u_dev, double rtol, pmg_batch* out) {
+  if (!out) return PMG_EINVAL;
+  *out = nullptr;
+  if (count < 1 || !hiers || !g_dev || !u_dev || !(rtol >= 0.0)) return PMG_EINVAL;
+  std::vector<Hier*> hs(count);
+  for (int i = 0; i < count; ++i) {
+    hs[i] = H(hiers[i]);
+    if (!hs[i] || !g_dev[i] || !u_dev[i]) return PMG_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return PMG_EINVAL;   // one workspace per concurrent solve
+  }
+  Batch* b = nullptr;
+  try {
+    b = new Batch();
+  } catch (...) {
+    return PMG_ENOMEM;
+  }
+  b->h = hs;
+  b->g.assign(g_dev, g_dev + count);
+  b->u.assign(u_dev, u_dev + count);
+  b->rtol = rtol;
+  b->fixed.assign(count, 0);
+  b->per_iter.assign(count, 0);
+  cudaGraph_t graph = nullptr;
+  int rc = PMG_OK;
+  try {
+    // one direct V-cycle per hierarchy that has not run yet (kernel set-up)
+    for (Hier* h : hs) {
+      if (h->pc_calls >= 1) continue;
+      PMG_CUDA(cudaMemsetAsync(h->r, 0, sizeof(double) * h->dims[h->L].ndof, 0));
+      precondition_graph(*h, 0);
+    }
+    PMG_CUDA(cudaStreamSynchronize(0));
+    b->dres = dev_alloc<SolveResult>(b->owned, count);
+    PMG_CUDA(cudaMallocHost(&b->hres, sizeof(SolveResult) * count));
+    PMG_CUDA(cudaGraphCreate(&graph, 0));
+    for (int i = 0; i < count; ++i)
+      capture_solve(*hs[i], graph, b->g[i], b->u[i], rtol, b->dres + i, &b->fixed[i],
+                    &b->per_iter[i]);
+    PMG_CUDA(cudaGraphInstantiate(&b->exec, graph, 0));
+  } catch (const CudaError& e) {
+    b->err = e.msg;
+    rc = e.code;
+  } catch (const std::bad_alloc&) {
+    rc = PMG_ENOMEM;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (rc != PMG_OK) {
+    std::fprintf(stderr, "pmg_batch_create: %s\n", b->err.c_str());
+    cudaGetLastError();
+    free_batch(b);
+    return rc;
+  }
+  *out = reinterpret_cast<pmg_batch>(b);
+  return PMG_OK;
+}
+
+int pmg_batch_solve(pmg_batch bb, pmg_stats* stats, void* stream) {
+  Batch* b = reinterpret_cast<Batch*>(bb);
+  if (!b) return PMG_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int count = (int)b->h.size();
+  int first_bad = PMG_OK;
+  try {
+    PMG_CUDA(cudaGraphLaunch(b->exec, s));
+    PMG_CUDA(cudaMemcpyAsync(b->hres, b->dres, sizeof(SolveResult) * count,
+                             cudaMemcpyDeviceToHost, s));
+    PMG_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < count; ++i) {
+      const SolveResult& r = b->hres[i];
+      g_launches.fetch_add(b->fixed[i] + (unsigned long long)r.iterations * b->per_iter[i],
+                           std::memory_order_relaxed);
+      if (stats) fill_stats(&stats[i], r, b->h[i]->hist, s);
+      if (first_bad == PMG_OK && r.status != PMG_OK) first_bad = r.status;
+    }
+  } catch (const CudaError& e) {
+    b->err = e.msg;
+    return e.code;
+  }
+  return first_bad;
+}
+
+void pmg_batch_destroy(pmg_batch bb) {
+  Batch* b = reinterpret_cast<Batch*>(bb);
+  if (!b) return;
+  cudaDeviceSynchronize();
+  free_batch(b);
+}
+
+const char* pmg_batch_last_error(pmg_batch bb) {
+  return bb ? reinterpret_cast<Batch*>(bb)->err.c_str() : "";
+}
+
+int pmg_hierarchy_autotune(pmg_hier hh, void* stream) {
+  Hier* h = H(hh);
+  if (!h) return PMG_EINVAL;
+  return guarded(h, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int l = 1; l <= h->L; ++l) {
+      if (h->opt.precision == PMG_PREC_FP64) tune_level<double>(*h, l, h->d64[l], s);
+      else tune_level<float>(*h, l, h->d32[l], s);
+    }
+    // captured graphs hold the old launch shapes: capture again on next use
+    if (h->sv_exec) cudaGraphExecDestroy(h->sv_exec);
+    h->sv_exec = nullptr;
+    if (h->sv_state == 1) h->sv_state = 0;
+    if (h->pc_exec) cudaGraphExecDestroy(h->pc_exec);
+    h->pc_exec = nullptr;
+    if (h->pc_state == 1) h->pc_state = 0;
+    return (int)PMG_OK;
+  });
+}
+
+int pmg_tuned_threads(pmg_hier hh, int level, int family) {
+  Hier* h = H(hh);
+  if (!h || level < 1 || level > h->L) return PMG_EINVAL;
+  const bool ea = h->opt.smoother == PMG_SMOOTHER_EA;
+  if (ea ? family != -1 : (family < 0 || family >= h->dims[level].dim)) return PMG_EINVAL;
+  if (h->opt.precision == PMG_PREC_FP64) {
+    const FdmFamily<double>& f = ea ? h->d64[level].ea : h->d64[level].fa[family];
+    return f.threads;
+  }
+  const FdmFamily<float>& f = ea ? h->d32[level].ea : h->d32[level].fa[family];
+  return f.threads;
+}
+
 const char* pmg_status_string(int status) {
   switch (status) {
     case PMG_OK: return "ok";
@@ -727,7 +1160,7 @@ int pmg_schwarz_sweep_native(pmg_hier hh, int level, int family, void* stream) {
   if (ea ? family != -1 : (family < 0 || family >= dm.dim)) return PMG_EINVAL;
   return guarded(h, [&] {
     cudaStream_t s = (cudaStream_t)stream;
-    if (h->opt.precision == PMG_PREC_MIXED) {
+    if (h->opt.precision != PMG_PREC_FP64) {
       LevelDev<float>& d = h->d32[level];
       PMG_CHECK(launch_fdm<float>(dm, ea ? d.ea : d.fa[family], d.f, d.u, s));
     } else {
@@ -786,7 +1219,7 @@ int pmg_schwarz_sweep(pmg_hier hh, int level, int family, const double* r, doubl
   if (ea ? family != -1 : (family < 0 || family >= dm.dim)) return PMG_EINVAL;
   return guarded(h, [&] {
     cudaStream_t s = (cudaStream_t)stream;
-    if (h->opt.precision == PMG_PREC_MIXED) {
+    if (h->opt.precision != PMG_PREC_FP64) {
       LevelDev<float>& d = h->d32[level];
       launch_convert<double, float>(r, d.r, dm.ndof, s);
       launch_convert<double, float>(u, d.u, dm.ndof, s);

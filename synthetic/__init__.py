@@ -175,3 +175,39 @@ def source_values(w: Workload, coords_1d: list) -> np.ndarray:
     if w.rhs == "gauss":
         return gauss_noise(w)
     raise ValueError(w.rhs)
+
+
+BATCH_SIDES = (8, 12, 16, 24)      # elements per axis of a batched grid
+BATCH_ORDERS = (4, 8, 16)          # P = 32 in 3-D is outside the library's 3-D range
+
+
+def config5(n_grids: int = 64, n_rhs: int = 4, budget_dof: int = 512_000_000,
+            grid_cap_dof: int = 64_000_000, seed: int = 0) -> list:
+    """Batched solves: n_grids independent 3-D Dirichlet grids on (0,1) x (0,ry) x (0,rz)
+    with n^3 elements, n drawn from BATCH_SIDES and P from BATCH_ORDERS; widths
+    hx = 1/n, hy = ry/n, hz = rz/n with ry, rz log-uniform in [1/4, 4], so element
+    aspect ratios span 1..16; n_rhs seeded Gaussian right-hand sides per grid.  The
+    device-memory budget caps the draws: a draw whose DOF x n_rhs exceeds grid_cap_dof,
+    or the remaining budget less what the grids still to draw need at the smallest
+    size, is rejected and redrawn; each accepted grid records its draw number in
+    `notes`."""
+    g = rng(seed)
+    out, left, draws = [], int(budget_dof), 0
+    smallest = min(BATCH_SIDES) ** 3 * (min(BATCH_ORDERS) + 1) ** 3 * n_rhs
+    while len(out) < n_grids:
+        draws += 1
+        if draws > 1000 * n_grids:
+            raise RuntimeError("batch budget too small for the requested number of grids")
+        n = int(g.choice(BATCH_SIDES))
+        P = int(g.choice(BATCH_ORDERS))
+        ry, rz = (float(v) for v in np.exp(g.uniform(math.log(0.25), math.log(4.0), size=2)))
+        dof = n ** 3 * (P + 1) ** 3
+        if dof * n_rhs > min(grid_cap_dof, left - (n_grids - len(out) - 1) * smallest):
+            continue
+        left -= dof * n_rhs
+        k = len(out)
+        out.append(Workload(f"batch{k:02d}_{n}cube_P{P}", 3, P, (n, n, n),
+                            [uniform_spacing(n, 1.0), uniform_spacing(n, ry), uniform_spacing(n, rz)],
+                            periodic=False, rhs="gauss", seed=seed * 100003 + k, notes=f"draw {draws}",
+                            extra={"n_rhs": n_rhs, "aspect": (1.0, ry, rz)}))
+    return out

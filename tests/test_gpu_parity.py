@@ -261,3 +261,21 @@ def test_per_level_parameters(kind):
     h.vcycle(to_dev(g2e(F, ne, P)), out)
     ref = g2e(oh.vcycle(np.zeros_like(F), F), ne, P)
     assert rel_err(from_dev(out, shape), ref) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_tc"])
+@pytest.mark.parametrize("kind", ["EA", "FA"])
+@pytest.mark.parametrize("case", [CASES[5], CASES[6], CASES[7], CASES[8]], ids=[IDS[5], IDS[6], IDS[7], IDS[8]])
+def test_mixed_precision_smoother_step(case, kind, precision):
+    """fp32 smoothing (SIMT, or tensor cores with the 3xTF32 split) against the FP64 oracle:
+    stated per-result error 1e-4 of the correction (fp32 residual and transforms)."""
+    dim, P, ne, sp, per, beta = case
+    g, h = make(case, smoother=kind, precision=precision)
+    for l in range(1, h.L + 1):
+        shape = elem_shape(dim, ne, 2 ** l)
+        u, f = rnd(shape, 60 + l), rnd(shape, 70 + l)
+        disc = dg.Discretisation(dim, 2 ** l, sp, per, beta, 1.0)
+        ref = g2e(schwarz.Smoother(disc, kind, "l", "quintic").step(e2g(u, dim), e2g(f, dim)), ne, 2 ** l)
+        ut = to_dev(u)
+        h.smooth(l, ut, to_dev(f), 1)
+        assert rel_err(from_dev(ut, shape) - u, ref - u) < 1e-4, (l, precision)
