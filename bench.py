@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2ldg", "c2x32", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c2",
+                    choices=["c1", "c2", "c2ldg", "c2x32", "c3", "c3s", "c4", "c5"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed_tc"],
@@ -86,6 +87,10 @@ def workload(name):
         return w, dict(smoother="EA", overlap="l")
     if name == "c3":
         return syn.config3(), dict(smoother="EA", overlap="l")
+    if name == "c3s":        # the P = 16 workload on 16^3 elements (20 M DOF): profiling
+        w = syn.config3()
+        w.name, w.n_elem, w.spacing = "poisson3d_16cube_P16_dirichlet_ip", (16, 16, 16), [syn.uniform_spacing(16, 1.0)] * 3
+        return w, dict(smoother="EA", overlap="l")
     if name == "c4":
         return syn.config4(), dict(smoother="FA", overlap="l", variable_v=True)
     raise ValueError(name)
