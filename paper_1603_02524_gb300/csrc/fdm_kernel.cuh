@@ -57,56 +57,22 @@ __device__ __forceinline__ void axpy_row(T* acc, const T* row, T x) {
   }
 }
 
-// General in-place line transform along an axis of length N: out_i = sum_a M[a][i] v_a,
+// Transform of one line held in registers.  General form: out_i = sum_a M[a][i] v_a,
 // M row-major with padded rows (forward: M = S, node-major; backward: M = W^T,
-// mode-major, so the same form applies W).  Each thread owns a line and keeps
-// all N partial sums in registers; long lines (N > 32) use dot products instead.
-template <typename T, int N>
-__device__ __forceinline__ void line_pass(T* buf, const T* M, int nlines, int lo_stride, int lo_count,
-                                          int hi_stride, int stride) {
-  constexpr int NP_ = padded<T>(N);
-  for (int l = threadIdx.x; l < nlines; l += blockDim.x) {
-    const int base = (l % lo_count) * lo_stride + (l / lo_count) * hi_stride;
-    T v[N];
-#pragma unroll
-    for (int a = 0; a < N; ++a) v[a] = buf[base + a * stride];
-    if constexpr (N <= 32) {
-      T acc[N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) acc[i] = T(0);
-#pragma unroll
-      for (int a = 0; a < N; ++a) axpy_row<T, N>(acc, M + a * NP_, v[a]);
-#pragma unroll
-      for (int i = 0; i < N; ++i) buf[base + i * stride] = acc[i];
-    } else {
-#pragma unroll 1
-      for (int i = 0; i < N; ++i) {
-        T s = T(0);
-#pragma unroll
-        for (int a = 0; a < N; ++a) s = fma(M[a * NP_ + i], v[a], s);
-        buf[base + i * stride] = s;
-      }
-    }
-  }
-}
-
-// Even-odd line transform (centro-symmetric axis).  Shared-memory layout: the
-// symmetric block (NE rows, padded) then the antisymmetric block (NO rows,
-// padded); NE = N - N/2, NO = N/2.  Forward: rows = nodes 0..NE-1 / 0..NO-1 of
-// S, output modes symmetric first (positions 0..NE-1) then antisymmetric.
-// Backward: rows = modes of W^T (transposed backward table), output nodes.
+// mode-major, so the same form applies W), all N partial sums in registers (long
+// lines, N > 32, use dot products instead).  Even-odd form on a centro-symmetric
+// axis: M holds the symmetric block (NE rows, padded) then the antisymmetric block
+// (NO rows, padded), NE = N - N/2, NO = N/2; forward: rows = nodes 0..NE-1 / 0..NO-1
+// of S, output modes symmetric first (positions 0..NE-1) then antisymmetric;
+// backward: rows = modes of W^T, output nodes.
 template <typename T, int N, bool FORWARD>
-__device__ __forceinline__ void line_pass_sym(T* buf, const T* M, int nlines, int lo_stride,
-                                              int lo_count, int hi_stride, int stride) {
-  constexpr int H = N / 2, NE = N - H, NO = H;
-  constexpr int PE = padded<T>(NE), PO = padded<T>(NO > 0 ? NO : 1);
-  const T* Me = M;
-  const T* Mo = M + NE * PE;
-  for (int l = threadIdx.x; l < nlines; l += blockDim.x) {
-    const int base = (l % lo_count) * lo_stride + (l / lo_count) * hi_stride;
-    T v[N];
-#pragma unroll
-    for (int a = 0; a < N; ++a) v[a] = buf[base + a * stride];
+__device__ __forceinline__ void line_transform(bool sym, const T* M, const T (&v)[N], T (&out)[N]) {
+  constexpr int NP_ = padded<T>(N);
+  if (N > 1 && N <= 32 && sym) {
+    constexpr int H = N / 2, NE = N - H, NO = H;
+    constexpr int PE = padded<T>(NE), PO = padded<T>(NO > 0 ? NO : 1);
+    const T* Me = M;
+    const T* Mo = M + NE * PE;
     T ae[NE], ao[NO > 0 ? NO : 1];
 #pragma unroll
     for (int i = 0; i < NE; ++i) ae[i] = T(0);
@@ -120,9 +86,9 @@ __device__ __forceinline__ void line_pass_sym(T* buf, const T* M, int nlines, in
       }
       if (NE > H) axpy_row<T, NE>(ae, Me + H * PE, v[H]);
 #pragma unroll
-      for (int i = 0; i < NE; ++i) buf[base + i * stride] = ae[i];
+      for (int i = 0; i < NE; ++i) out[i] = ae[i];
 #pragma unroll
-      for (int i = 0; i < NO; ++i) buf[base + (NE + i) * stride] = ao[i];
+      for (int i = 0; i < NO; ++i) out[NE + i] = ao[i];
     } else {
 #pragma unroll
       for (int i = 0; i < NE; ++i) axpy_row<T, NE>(ae, Me + i * PE, v[i]);
@@ -130,19 +96,68 @@ __device__ __forceinline__ void line_pass_sym(T* buf, const T* M, int nlines, in
       for (int i = 0; i < NO; ++i) axpy_row<T, NO>(ao, Mo + i * PO, v[NE + i]);
 #pragma unroll
       for (int a = 0; a < H; ++a) {
-        buf[base + a * stride] = ae[a] + ao[a];
-        buf[base + (N - 1 - a) * stride] = ae[a] - ao[a];
+        out[a] = ae[a] + ao[a];
+        out[N - 1 - a] = ae[a] - ao[a];
       }
-      if (NE > H) buf[base + H * stride] = ae[H];
+      if (NE > H) out[H] = ae[H];
+    }
+  } else if constexpr (N <= 32) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = T(0);
+#pragma unroll
+    for (int a = 0; a < N; ++a) axpy_row<T, N>(out, M + a * NP_, v[a]);
+  } else {
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+      T s = T(0);
+#pragma unroll
+      for (int a = 0; a < N; ++a) s = fma(M[a * NP_ + i], v[a], s);
+      out[i] = s;
     }
   }
 }
 
-template <typename T, int N, bool FORWARD>
+// 1 / s: hardware single-precision approximate reciprocal (rcp.approx, relative
+// error about 2^-23); in double refined by Newton's iteration x <- x + x (1 - s x),
+// each step squaring the relative error (2^-22 -> 2^-44 -> below double rounding).
+// The double <-> float moves are bit-level (dfloat.cuh): on GB300 a cvt between
+// double and float costs as much as an FP64 multiply-add.
+__device__ __forceinline__ float rcp_approx(float s) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
+  return r;
+}
+__device__ __forceinline__ double recip(double s) {
+  double x = widen(rcp_approx(split_double(s).hi));
+  double e = fma(-s, x, 1.0);
+  x = fma(x, e, x);
+  e = fma(-s, x, 1.0);
+  return fma(x, e, x);
+}
+__device__ __forceinline__ float recip(float s) { return rcp_approx(s); }
+
+// One in-place pass over all lines of an axis: line l starts at
+// (l % lo_count) * lo_stride + (l / lo_count) * hi_stride, nodes `stride` apart.
+// SCALE (the last forward pass): output i of line l is multiplied by
+// 1 / (lsum(l) + lq[i]), the inverse eigenvalue sum of the fast diagonalisation.
+template <typename T, int N, bool FORWARD, bool SCALE = false, typename LS = int>
 __device__ __forceinline__ void axis_pass(bool sym, T* buf, const T* M, int nlines, int lo_stride,
-                                          int lo_count, int hi_stride, int stride) {
-  if (N > 1 && N <= 32 && sym) line_pass_sym<T, N, FORWARD>(buf, M, nlines, lo_stride, lo_count, hi_stride, stride);
-  else line_pass<T, N>(buf, M, nlines, lo_stride, lo_count, hi_stride, stride);
+                                          int lo_count, int hi_stride, int stride,
+                                          const T* lq = nullptr, LS lsum = LS()) {
+  for (int l = threadIdx.x; l < nlines; l += blockDim.x) {
+    const int base = (l % lo_count) * lo_stride + (l / lo_count) * hi_stride;
+    T v[N], out[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) v[a] = buf[base + a * stride];
+    line_transform<T, N, FORWARD>(sym, M, v, out);
+    if constexpr (SCALE) {
+      const T s0 = lsum(l);
+#pragma unroll
+      for (int i = 0; i < N; ++i) out[i] *= recip(s0 + lq[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) buf[base + i * stride] = out[i];
+  }
 }
 
 // Copy an n x n table (general, row-major) or its even-odd folded blocks from
@@ -261,17 +276,7 @@ __host__ __device__ constexpr int table_floats(int n) {
   return TC ? (n + 7) / 8 * 8 * ((n + 7) / 8 * 8) : n * padded<T>(n);
 }
 
-// 1 / s: hardware single-precision reciprocal refined by Newton's iteration
-// x <- x (2 - s x), written as x <- x + x (1 - s x); each step squares the
-// relative error (2^-23 -> 2^-46 -> below double rounding).
-__device__ __forceinline__ double recip(double s) {
-  double x = (double)__frcp_rn((float)s);
-  double e = fma(-s, x, 1.0);
-  x = fma(x, e, x);
-  e = fma(-s, x, 1.0);
-  return fma(x, e, x);
-}
-__device__ __forceinline__ float recip(float s) { return __frcp_rn(s); }
+
 
 // Default CTA size: enough threads for the widest line pass (one line per
 // thread), rounded to whole warps, at most 256.
@@ -300,8 +305,15 @@ __device__ __forceinline__ void tload(T* dst, const T* src, bool sym) {
   else load_table<T, N>(dst, src, sym);
 }
 
+// Largest CTA of a shape: kFdmMaxThreads (registers capped at 128 per thread), or
+// 256 for FP64 patches with 32-node axes, whose lines need more registers.
+template <typename T, int NA, int NB, int NC>
+constexpr int fdm_max_threads() {
+  return (sizeof(T) == 8 && (NA >= 32 || NB >= 32 || NC >= 32)) ? 256 : kFdmMaxThreads;
+}
+
 template <typename T, int NA, int NB, int NC, bool TC>
-__global__ void __launch_bounds__(kFdmMaxThreads)
+__global__ void __launch_bounds__(fdm_max_threads<T, NA, NB, NC>())
 fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restrict__ u) {
   static_assert(!TC || (sizeof(T) == 4 && NA <= 32 && NB <= 32 && NC <= 32 && NC > 1),
                 "tensor-core passes: fp32, 3-D, at most 32 nodes per axis");
@@ -377,18 +389,31 @@ fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restric
   }
   __syncthreads();
 
-  // forward transforms
+  // forward transforms, then the scaling by 1 / (lambda_a + lambda_b + lambda_c)
+  // (SIMT: folded into the last forward pass)
   pass<T, NA, true, TC>(sym[0], buf, Sq[0], NB * NC, NA, NB * NC, 0, 1);
   __syncthreads();
-  pass<T, NB, true, TC>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA);
-  __syncthreads();
-  if (NC > 1) {
-    pass<T, NC, true, TC>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB);
+  if constexpr (TC) {
+    pass<T, NB, true, TC>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA);
     __syncthreads();
-  }
-  for (int t = threadIdx.x; t < NN; t += blockDim.x) {
-    const int a = t % NA, b = (t / NA) % NB, c = t / (NA * NB);
-    buf[t] *= recip(la[a] + lb[b] + lc[c]);
+    if (NC > 1) {
+      pass<T, NC, true, TC>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB);
+      __syncthreads();
+    }
+    for (int t = threadIdx.x; t < NN; t += blockDim.x) {
+      const int a = t % NA, b = (t / NA) % NB, c = t / (NA * NB);
+      buf[t] *= recip(la[a] + lb[b] + lc[c]);
+    }
+  } else if constexpr (NC > 1) {
+    axis_pass<T, NB, true>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA);
+    __syncthreads();
+    // line l = (a, b) = (l % NA, l / NA), outputs along c
+    axis_pass<T, NC, true, true>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB, lc,
+                                 [&](int l) { return la[l % NA] + lb[l / NA]; });
+  } else {
+    // 2-D: line l = (a, c) = (l % NA, l / NA), outputs along b
+    axis_pass<T, NB, true, true>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA, lb,
+                                 [&](int l) { return la[l % NA] + lc[l / NA]; });
   }
   __syncthreads();
   if (NC > 1) {
@@ -427,8 +452,9 @@ int fdm_launch(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, c
   }
   attr_done = true;
   if (fam.count_total <= 0) return PMG_OK;
-  const int threads = (fam.threads >= 32 && fam.threads <= kFdmMaxThreads && fam.threads % 32 == 0)
-                          ? fam.threads : fdm_threads<NA, NB, NC>();
+  constexpr int maxt = fdm_max_threads<T, NA, NB, NC>();
+  int threads = (fam.threads >= 32 && fam.threads % 32 == 0) ? fam.threads : fdm_threads<NA, NB, NC>();
+  if (threads > maxt) threads = maxt;
   count_launch();
   fdm_kernel<T, NA, NB, NC, TC><<<fam.count_total, threads, smem, s>>>(dm, fam, r, u);
   return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
