@@ -63,6 +63,14 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
   const long long e0 = (long long)blockIdx.x * S::EPB;
   const long long nodes_blk = (long long)S::EPB * S::NODES;
   const long long total = dm.nelem * S::NODES;
+  // element coordinates of the block's elements (one 64-bit division set per element)
+  __shared__ int s_me[S::EPB][3];
+  if (tid < S::EPB) {
+    const long long ee = e0 + tid;
+    s_me[tid][0] = (int)(ee % dm.ne[0]);
+    s_me[tid][1] = (int)((ee / dm.ne[0]) % dm.ne[1]);
+    s_me[tid][2] = (int)(ee / ((long long)dm.ne[0] * dm.ne[1]));
+  }
   for (int t = tid; t < nodes_blk; t += blockDim.x) {
     long long g = e0 * S::NODES + t;
     su[t] = g < total ? T(u[g]) : T(0);
@@ -74,9 +82,9 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
   const bool active = (el < S::EPB) && (e < dm.nelem);
   int me[3] = {0, 0, 0};
   if (active) {
-    me[0] = (int)(e % dm.ne[0]);
-    me[1] = (int)((e / dm.ne[0]) % dm.ne[1]);
-    me[2] = (int)(e / ((long long)dm.ne[0] * dm.ne[1]));
+    me[0] = s_me[el][0];
+    me[1] = s_me[el][1];
+    me[2] = s_me[el][2];
   }
   T* sel = su + el * S::NODES;
   T* ael = acc + el * S::NODES;
@@ -177,14 +185,14 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
   for (int t = tid; t < nodes_blk; t += blockDim.x) {
     long long g = e0 * S::NODES + t;
     if (g >= total) continue;
-    const long long ee = g / S::NODES;
-    const int nd = (int)(g % S::NODES);
+    const int le = t / S::NODES;
+    const int nd = t - le * S::NODES;
     const int i = nd % NP, j = (nd / NP) % NP;
-    const int mx = (int)(ee % dm.ne[0]), my = (int)((ee / dm.ne[0]) % dm.ne[1]);
+    const int mx = s_me[le][0], my = s_me[le][1];
     T m = ldg(at.M[0] + (size_t)mx * NP + i) * ldg(at.M[1] + (size_t)my * NP + j);
     if (DIM == 3) {
       const int k = nd / (NP * NP);
-      const int mz = (int)(ee / ((long long)dm.ne[0] * dm.ne[1]));
+      const int mz = s_me[le][2];
       m = m * ldg(at.M[2] + (size_t)mz * NP + k);
     }
     const T val = m * acc[t];

@@ -320,7 +320,8 @@ fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restric
   constexpr int NN = NA * NB * NC;
   extern __shared__ __align__(16) unsigned char fdm_smem[];
   long long* off = reinterpret_cast<long long*>(fdm_smem);        // NA + NB + NC
-  T* buf = reinterpret_cast<T*>(off + (NA + NB + NC + 1) / 2 * 2);
+  long long* rowoff = off + (NA + NB + NC + 1) / 2 * 2;             // NB * NC row offsets
+  T* buf = reinterpret_cast<T*>(rowoff + (NB * NC + 1) / 2 * 2);
   T* Sq[3];
   T* Wq[3];
   Sq[0] = buf + padded<T>(NN);
@@ -381,10 +382,14 @@ fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restric
     }
   }
   __syncthreads();
+  // offset of each row (b, c) of the patch buffer (negative: outside the grid)
+  for (int rr = threadIdx.x; rr < NB * NC; rr += blockDim.x)
+    rowoff[rr] = off[NA + rr % NB] + off[NA + NB + rr / NB];
+  __syncthreads();
 
   for (int t = threadIdx.x; t < NN; t += blockDim.x) {
-    const int a = t % NA, b = (t / NA) % NB, c = t / (NA * NB);
-    const long long o = off[a] + off[NA + b] + off[NA + NB + c];
+    const int row = t / NA, a = t - row * NA;
+    const long long o = off[a] + rowoff[row];
     buf[t] = o >= 0 ? r[o] : T(0);
   }
   __syncthreads();
@@ -426,15 +431,15 @@ fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restric
   __syncthreads();
 
   for (int t = threadIdx.x; t < NN; t += blockDim.x) {
-    const int a = t % NA, b = (t / NA) % NB, c = t / (NA * NB);
-    const long long o = off[a] + off[NA + b] + off[NA + NB + c];
+    const int row = t / NA, a = t - row * NA;
+    const long long o = off[a] + rowoff[row];
     if (o >= 0) atomicAdd(u + o, buf[t]);
   }
 }
 
 template <typename T, int NA, int NB, int NC, bool TC>
 constexpr size_t fdm_smem_bytes() {
-  return sizeof(long long) * ((NA + NB + NC + 1) / 2 * 2) +
+  return sizeof(long long) * ((NA + NB + NC + 1) / 2 * 2 + (NB * NC + 1) / 2 * 2) +
          sizeof(T) * ((size_t)padded<T>(NA * NB * NC) +
                       2 * (table_floats<T, TC>(NA) + table_floats<T, TC>(NB) + table_floats<T, TC>(NC)) +
                       NA + NB + NC);
