@@ -496,11 +496,11 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
     peak = (FP64_PEAK_GFLOPS if fp64_main else FP32_PEAK_GFLOPS) / 1e3
     ach = flops / (ms * 1e-3) / 1e12
     # DRAM bytes per patch of this kernel from one ncu capture of the same kernel on the
-    # 32^3-element P = 8 problem (profiles/fdm_kernel_double_13_poisson3d_32cube_P8.md),
+    # 32^3-element P = 8 problem (the ncu summary of fdm_kernel<double,13> under profiles/),
     # scaled by patches; only for the kernel version that was captured
     traffic = None
     if fam == -1 and fp64_main and w.P == 8 and w.dim == 3:
-        traffic = (382.78e6 + 153.36e6) / 32768 * nelem
+        traffic = (383.11e6 + 152.65e6) / 32768 * nelem
     line["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                         "frac": ach / peak, "traffic": traffic,
                         "kernel": (f"fdm_kernel<{tname},{nn},{nn},{nn}> (EA patch solve, P={w.P})"
