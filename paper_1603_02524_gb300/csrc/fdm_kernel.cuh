@@ -305,6 +305,58 @@ __device__ __forceinline__ void tload(T* dst, const T* src, bool sym) {
   else load_table<T, N>(dst, src, sym);
 }
 
+// The patch solve proper on a staged patch: three forward line passes (the last
+// one scaled by the inverse eigenvalue sums), three backward passes, and the
+// weighted corrections added to u (atomically: patches overlap).
+template <typename T, int NA, int NB, int NC, bool TC>
+__device__ __forceinline__ void patch_compute(T* buf, T* const (&Sq)[3], T* const (&Wq)[3], const T* la,
+                                              const T* lb, const T* lc, const bool (&sym)[3],
+                                              const long long* off, const long long* rowoff,
+                                              T* __restrict__ u) {
+  constexpr int NN = NA * NB * NC;
+  // forward transforms, then the scaling by 1 / (lambda_a + lambda_b + lambda_c)
+  // (SIMT: folded into the last forward pass)
+  pass<T, NA, true, TC>(sym[0], buf, Sq[0], NB * NC, NA, NB * NC, 0, 1);
+  __syncthreads();
+  if constexpr (TC) {
+    pass<T, NB, true, TC>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA);
+    __syncthreads();
+    if (NC > 1) {
+      pass<T, NC, true, TC>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB);
+      __syncthreads();
+    }
+    for (int t = threadIdx.x; t < NN; t += blockDim.x) {
+      const int a = t % NA, b = (t / NA) % NB, c = t / (NA * NB);
+      buf[t] *= recip(la[a] + lb[b] + lc[c]);
+    }
+  } else if constexpr (NC > 1) {
+    axis_pass<T, NB, true>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA);
+    __syncthreads();
+    // line l = (a, b) = (l % NA, l / NA), outputs along c
+    axis_pass<T, NC, true, true>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB, lc,
+                                 [&](int l) { return la[l % NA] + lb[l / NA]; });
+  } else {
+    // 2-D: line l = (a, c) = (l % NA, l / NA), outputs along b
+    axis_pass<T, NB, true, true>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA, lb,
+                                 [&](int l) { return la[l % NA] + lc[l / NA]; });
+  }
+  __syncthreads();
+  if (NC > 1) {
+    pass<T, NC, false, TC>(sym[2], buf, Wq[2], NA * NB, 1, NA * NB, 0, NA * NB);
+    __syncthreads();
+  }
+  pass<T, NB, false, TC>(sym[1], buf, Wq[1], NA * NC, 1, NA, NA * NB, NA);
+  __syncthreads();
+  pass<T, NA, false, TC>(sym[0], buf, Wq[0], NB * NC, NA, NB * NC, 0, 1);
+  __syncthreads();
+
+  for (int t = threadIdx.x; t < NN; t += blockDim.x) {
+    const int row = t / NA, a = t - row * NA;
+    const long long o = off[a] + rowoff[row];
+    if (o >= 0) atomicAdd(u + o, buf[t]);
+  }
+}
+
 // Largest CTA of a shape: kFdmMaxThreads (registers capped at 128 per thread), or
 // 256 for FP64 patches with 32-node axes, whose lines need more registers.
 template <typename T, int NA, int NB, int NC>
@@ -394,46 +446,167 @@ fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restric
   }
   __syncthreads();
 
-  // forward transforms, then the scaling by 1 / (lambda_a + lambda_b + lambda_c)
-  // (SIMT: folded into the last forward pass)
-  pass<T, NA, true, TC>(sym[0], buf, Sq[0], NB * NC, NA, NB * NC, 0, 1);
-  __syncthreads();
-  if constexpr (TC) {
-    pass<T, NB, true, TC>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA);
-    __syncthreads();
-    if (NC > 1) {
-      pass<T, NC, true, TC>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB);
-      __syncthreads();
-    }
-    for (int t = threadIdx.x; t < NN; t += blockDim.x) {
-      const int a = t % NA, b = (t / NA) % NB, c = t / (NA * NB);
-      buf[t] *= recip(la[a] + lb[b] + lc[c]);
-    }
-  } else if constexpr (NC > 1) {
-    axis_pass<T, NB, true>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA);
-    __syncthreads();
-    // line l = (a, b) = (l % NA, l / NA), outputs along c
-    axis_pass<T, NC, true, true>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB, lc,
-                                 [&](int l) { return la[l % NA] + lb[l / NA]; });
-  } else {
-    // 2-D: line l = (a, c) = (l % NA, l / NA), outputs along b
-    axis_pass<T, NB, true, true>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA, lb,
-                                 [&](int l) { return la[l % NA] + lc[l / NA]; });
-  }
-  __syncthreads();
-  if (NC > 1) {
-    pass<T, NC, false, TC>(sym[2], buf, Wq[2], NA * NB, 1, NA * NB, 0, NA * NB);
-    __syncthreads();
-  }
-  pass<T, NB, false, TC>(sym[1], buf, Wq[1], NA * NC, 1, NA, NA * NB, NA);
-  __syncthreads();
-  pass<T, NA, false, TC>(sym[0], buf, Wq[0], NB * NC, NA, NB * NC, 0, 1);
-  __syncthreads();
+  patch_compute<T, NA, NB, NC, TC>(buf, Sq, Wq, la, lb, lc, sym, off, rowoff, u);
+}
 
-  for (int t = threadIdx.x; t < NN; t += blockDim.x) {
+// ---------------------------------------------------------------------------
+// Pipelined form (fp32 SIMT, shapes whose two stages fit twice per SM): a
+// persistent CTA walks over patches p, p + gridDim.x, ...; while it computes
+// one patch, the gather of the next patch (residual values, eigen-tables,
+// eigenvalues) is already in flight as cp.async copies into the other stage,
+// so the long-latency loads of one patch overlap the line passes of another.
+// ---------------------------------------------------------------------------
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(BYTES),
+               "r"(valid ? BYTES : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// table copy of load_table as asynchronous element copies (row padding left unset:
+// the line passes never read it)
+template <typename T, int N>
+__device__ __forceinline__ void load_table_async(T* dst, const T* src, bool sym) {
+  constexpr int NP_ = padded<T>(N);
+  constexpr int H = N / 2, NE = N - H, NO = H;
+  constexpr int PE = padded<T>(NE), PO = padded<T>(NO > 0 ? NO : 1);
+  if (sym && N > 1 && N <= 32) {
+    for (int t = threadIdx.x; t < NE * NE; t += blockDim.x)
+      cp_async<sizeof(T)>(dst + (t / NE) * PE + t % NE, src + t, true);
+    for (int t = threadIdx.x; t < NO * NO; t += blockDim.x)
+      cp_async<sizeof(T)>(dst + NE * PE + (t / NO) * PO + t % NO, src + NE * NE + t, true);
+  } else {
+    for (int t = threadIdx.x; t < N * N; t += blockDim.x)
+      cp_async<sizeof(T)>(dst + (t / N) * NP_ + t % N, src + t, true);
+  }
+}
+
+// one stage: offsets, row offsets, symmetry flags, patch buffer, six tables, eigenvalues
+template <typename T, int NA, int NB, int NC>
+struct PipeStage {
+  static constexpr int NN = NA * NB * NC;
+  static constexpr size_t OFF = 0;
+  static constexpr size_t ROW = OFF + 8 * (size_t)((NA + NB + NC + 1) / 2 * 2);
+  static constexpr size_t SYM = ROW + 8 * (size_t)((NB * NC + 1) / 2 * 2);
+  static constexpr size_t BUF = SYM + 16;
+  static constexpr size_t TBL = BUF + sizeof(T) * (size_t)padded<T>(NN);
+  static constexpr size_t LAM = TBL + sizeof(T) * 2 * (size_t)(table_floats<T, false>(NA) +
+                                                               table_floats<T, false>(NB) +
+                                                               table_floats<T, false>(NC));
+  static constexpr size_t END = LAM + sizeof(T) * (size_t)((NA + NB + NC + 3) / 4 * 4);
+  static constexpr size_t BYTES = (END + 15) / 16 * 16;
+};
+
+template <typename T, int NA, int NB, int NC, bool TC>
+constexpr bool fdm_pipelined() {
+  return !TC && sizeof(T) == 4 && 2 * PipeStage<T, NA, NB, NC>::BYTES <= 100 * 1024;
+}
+
+// Offsets of patch pid (plain stores, then two barriers), then its gather and
+// tables as one cp.async group.  Every thread of the CTA calls it.
+template <typename T, int NA, int NB, int NC>
+__device__ __forceinline__ void pipe_prepare(const LevelDims& dm, const FdmFamily<T>& fam,
+                                             const T* __restrict__ r, unsigned char* st, int pid) {
+  using PS = PipeStage<T, NA, NB, NC>;
+  long long* off = reinterpret_cast<long long*>(st + PS::OFF);
+  long long* rowoff = reinterpret_cast<long long*>(st + PS::ROW);
+  int* sym = reinterpret_cast<int*>(st + PS::SYM);
+  T* buf = reinterpret_cast<T*>(st + PS::BUF);
+  T* tb = reinterpret_cast<T*>(st + PS::TBL);
+  T* lam = reinterpret_cast<T*>(st + PS::LAM);
+  const int ca = fam.ax[0].count, cb = fam.ax[1].count;
+  const int pidx[3] = {pid % ca, (pid / ca) % cb, pid / (ca * cb)};
+  const int nq[3] = {NA, NB, NC};
+  const int base[3] = {0, NA, NA + NB};
+  const long long nodes_el = (long long)dm.NP * dm.NP * dm.NPz;
+  const long long estride[3] = {nodes_el, nodes_el * dm.ne[0], nodes_el * dm.ne[0] * dm.ne[1]};
+  const long long nstride[3] = {1, dm.NP, (long long)dm.NP * dm.NP};
+  if (threadIdx.x < 3) sym[threadIdx.x] = fam.ax[threadIdx.x].sym[pidx[threadIdx.x]] != 0;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const FdmAxis<T>& ax = fam.ax[q];
+    const int n = nq[q];
+    if (threadIdx.x < n) {
+      const int a = threadIdx.x;
+      const size_t p = pidx[q];
+      cp_async<sizeof(T)>(lam + base[q] + a, ax.lam + p * n + a, true);
+      const int ph = ax.phys;
+      const int npp = (ph == 2) ? dm.NPz : dm.NP;
+      int G = ax.start0 + (int)p * npp + a;
+      long long o;
+      if (ax.periodic) {
+        G %= ax.N;
+        if (G < 0) G += ax.N;
+        o = (long long)(G / npp) * estride[ph] + (G % npp) * nstride[ph];
+      } else if (G < 0 || G >= ax.N) {
+        o = kInvalidOffset;
+      } else {
+        o = (long long)(G / npp) * estride[ph] + (G % npp) * nstride[ph];
+      }
+      off[base[q] + a] = o;
+    }
+  }
+  __syncthreads();
+  for (int rr = threadIdx.x; rr < NB * NC; rr += blockDim.x)
+    rowoff[rr] = off[NA + rr % NB] + off[NA + NB + rr / NB];
+  __syncthreads();
+  for (int t = threadIdx.x; t < PS::NN; t += blockDim.x) {
     const int row = t / NA, a = t - row * NA;
     const long long o = off[a] + rowoff[row];
-    if (o >= 0) atomicAdd(u + o, buf[t]);
+    cp_async<sizeof(T)>(buf + t, o >= 0 ? r + o : r, o >= 0);
+  }
+  T* S0 = tb;
+  T* W0 = S0 + table_floats<T, false>(NA);
+  T* S1 = W0 + table_floats<T, false>(NA);
+  T* W1 = S1 + table_floats<T, false>(NB);
+  T* S2 = W1 + table_floats<T, false>(NB);
+  T* W2 = S2 + table_floats<T, false>(NC);
+  {
+    const size_t p0 = pidx[0], p1 = pidx[1], p2 = pidx[2];
+    load_table_async<T, NA>(S0, fam.ax[0].S + p0 * NA * NA, sym[0]);
+    load_table_async<T, NA>(W0, fam.ax[0].W + p0 * NA * NA, sym[0]);
+    load_table_async<T, NB>(S1, fam.ax[1].S + p1 * NB * NB, sym[1]);
+    load_table_async<T, NB>(W1, fam.ax[1].W + p1 * NB * NB, sym[1]);
+    load_table_async<T, NC>(S2, fam.ax[2].S + p2 * NC * NC, sym[2]);
+    load_table_async<T, NC>(W2, fam.ax[2].W + p2 * NC * NC, sym[2]);
+  }
+  cp_async_commit();
+}
+
+template <typename T, int NA, int NB, int NC>
+__global__ void __launch_bounds__(fdm_max_threads<T, NA, NB, NC>())
+fdm_kernel_pipe(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restrict__ u) {
+  using PS = PipeStage<T, NA, NB, NC>;
+  extern __shared__ __align__(16) unsigned char fdm_smem[];
+  const int count = fam.count_total;
+  int p = blockIdx.x;
+  if (p >= count) return;
+  pipe_prepare<T, NA, NB, NC>(dm, fam, r, fdm_smem, p);
+  int s = 0;
+  for (; p < count; p += gridDim.x) {
+    const int pn = p + gridDim.x;
+    if (pn < count) pipe_prepare<T, NA, NB, NC>(dm, fam, r, fdm_smem + (s ^ 1) * PS::BYTES, pn);
+    else cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    unsigned char* st = fdm_smem + s * PS::BYTES;
+    T* tb = reinterpret_cast<T*>(st + PS::TBL);
+    T* const Sq[3] = {tb, tb + 2 * table_floats<T, false>(NA),
+                      tb + 2 * (table_floats<T, false>(NA) + table_floats<T, false>(NB))};
+    T* const Wq[3] = {Sq[0] + table_floats<T, false>(NA), Sq[1] + table_floats<T, false>(NB),
+                      Sq[2] + table_floats<T, false>(NC)};
+    const T* lam = reinterpret_cast<const T*>(st + PS::LAM);
+    const int* sy = reinterpret_cast<const int*>(st + PS::SYM);
+    const bool sym[3] = {sy[0] != 0, sy[1] != 0, sy[2] != 0};
+    patch_compute<T, NA, NB, NC, false>(reinterpret_cast<T*>(st + PS::BUF), Sq, Wq, lam, lam + NA,
+                                        lam + NA + NB, sym, reinterpret_cast<const long long*>(st + PS::OFF),
+                                        reinterpret_cast<const long long*>(st + PS::ROW), u);
+    __syncthreads();
+    s ^= 1;
   }
 }
 
@@ -447,6 +620,36 @@ constexpr size_t fdm_smem_bytes() {
 
 template <typename T, int NA, int NB, int NC, bool TC = false>
 int fdm_launch(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, cudaStream_t s) {
+  if constexpr (fdm_pipelined<T, NA, NB, NC, TC>()) {
+    constexpr size_t smem2 = 2 * PipeStage<T, NA, NB, NC>::BYTES;
+    constexpr int maxt = fdm_max_threads<T, NA, NB, NC>();
+    static bool attr2 = false;
+    static int nsm = 0;
+    static int per_sm[maxt / 32 + 1] = {};
+    if (!attr2) {
+      if (smem2 > 48 * 1024 &&
+          cudaFuncSetAttribute(fdm_kernel_pipe<T, NA, NB, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem2) != cudaSuccess)
+        return PMG_ECUDA;
+      int dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return PMG_ECUDA;
+      attr2 = true;
+    }
+    if (fam.count_total <= 0) return PMG_OK;
+    int threads = (fam.threads >= 32 && fam.threads % 32 == 0) ? fam.threads : fdm_threads<NA, NB, NC>();
+    if (threads > maxt) threads = maxt;
+    int& occ = per_sm[threads / 32];
+    if (occ <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fdm_kernel_pipe<T, NA, NB, NC>, threads,
+                                                                  smem2) != cudaSuccess)
+      return PMG_ECUDA;
+    long long grid = (long long)(occ > 0 ? occ : 1) * nsm;
+    if (grid > fam.count_total) grid = fam.count_total;
+    count_launch();
+    fdm_kernel_pipe<T, NA, NB, NC><<<(unsigned)grid, threads, smem2, s>>>(dm, fam, r, u);
+    return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
+  }
   constexpr size_t smem = fdm_smem_bytes<T, NA, NB, NC, TC>();
   static_assert(smem <= 227 * 1024, "patch does not fit in shared memory");
   static bool attr_done = false;
