@@ -501,9 +501,16 @@ struct PipeStage {
   static constexpr size_t BYTES = (END + 15) / 16 * 16;
 };
 
+// The pipelined form exists for fp32 SIMT shapes whose two stages fit one CTA;
+// by default it runs where two such CTAs fit an SM, and the autotuner may choose
+// either form (FdmFamily::variant).
 template <typename T, int NA, int NB, int NC, bool TC>
 constexpr bool fdm_pipelined() {
-  return !TC && sizeof(T) == 4 && 2 * PipeStage<T, NA, NB, NC>::BYTES <= 100 * 1024;
+  return !TC && sizeof(T) == 4 && 2 * PipeStage<T, NA, NB, NC>::BYTES <= 226 * 1024;
+}
+template <typename T, int NA, int NB, int NC>
+constexpr bool fdm_pipelined_default() {
+  return 2 * PipeStage<T, NA, NB, NC>::BYTES <= 100 * 1024;
 }
 
 // Offsets of patch pid (plain stores, then two barriers), then its gather and
@@ -620,7 +627,10 @@ constexpr size_t fdm_smem_bytes() {
 
 template <typename T, int NA, int NB, int NC, bool TC = false>
 int fdm_launch(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, cudaStream_t s) {
-  if constexpr (fdm_pipelined<T, NA, NB, NC, TC>()) {
+  bool pipe = false;
+  if constexpr (fdm_pipelined<T, NA, NB, NC, TC>())
+    pipe = fam.variant < 0 ? fdm_pipelined_default<T, NA, NB, NC>() : fam.variant == 1;
+  if constexpr (fdm_pipelined<T, NA, NB, NC, TC>()) if (pipe) {
     constexpr size_t smem2 = 2 * PipeStage<T, NA, NB, NC>::BYTES;
     constexpr int maxt = fdm_max_threads<T, NA, NB, NC>();
     static bool attr2 = false;

@@ -92,6 +92,7 @@ struct FdmFamily {
   int count_total;
   int tc = 0;          // fp32 only: 1 = line passes on the tensor cores (tables unfolded)
   int threads = 0;     // CTA size chosen by the autotuner (0: the kernel's default)
+  int variant = -1;    // fp32: 0 one patch per CTA, 1 pipelined persistent CTAs, -1 default
 };
 
 struct LevelDims {

@@ -511,7 +511,10 @@ int tune_family(Hier& h, int l, FdmFamily<T>& fam, LevelDev<T>& d, cudaStream_t 
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
-    if (it != g_tune_cache.end()) return fam.threads = it->second;
+    if (it != g_tune_cache.end()) {
+      fam.variant = it->second / 1000;
+      return fam.threads = it->second % 1000;
+    }
   }
   const LevelDims& dm = h.dims[l];
   PMG_CUDA(cudaMemsetAsync(d.f, 0, sizeof(T) * dm.ndof, s));
@@ -520,35 +523,43 @@ int tune_family(Hier& h, int l, FdmFamily<T>& fam, LevelDev<T>& d, cudaStream_t 
   cudaEvent_t e0, e1;
   PMG_CUDA(cudaEventCreate(&e0));
   PMG_CUDA(cudaEventCreate(&e1));
-  int best = 0;
+  int best = 0, best_v = -1;
   float best_ms = 1e30f;
+  // fp32 families: both kernel forms (one patch per CTA, pipelined persistent CTAs)
+  const int nvar = sizeof(T) == 4 && !fam.tc ? 2 : 1;
   try {
-    for (int c : cand) {
-      if (c > kFdmMaxThreads) continue;
-      fam.threads = c;
-      PMG_CHECK(launch_fdm<T>(dm, fam, d.f, d.u, s));            // warm-up
-      PMG_CUDA(cudaEventRecord(e0, s));
-      for (int rep = 0; rep < 3; ++rep) PMG_CHECK(launch_fdm<T>(dm, fam, d.f, d.u, s));
-      PMG_CUDA(cudaEventRecord(e1, s));
-      PMG_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.0f;
-      PMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = c;
+    for (int v = 0; v < nvar; ++v) {
+      for (int c : cand) {
+        if (c > kFdmMaxThreads) continue;
+        fam.threads = c;
+        fam.variant = nvar == 2 ? v : -1;
+        PMG_CHECK(launch_fdm<T>(dm, fam, d.f, d.u, s));            // warm-up
+        PMG_CUDA(cudaEventRecord(e0, s));
+        for (int rep = 0; rep < 3; ++rep) PMG_CHECK(launch_fdm<T>(dm, fam, d.f, d.u, s));
+        PMG_CUDA(cudaEventRecord(e1, s));
+        PMG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        PMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = c;
+          best_v = fam.variant;
+        }
       }
     }
   } catch (...) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     fam.threads = 0;
+    fam.variant = -1;
     throw;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   fam.threads = best;
+  fam.variant = best_v;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune_cache[key] = best;
+  g_tune_cache[key] = best + 1000 * (best_v < 0 ? 0 : best_v);
   return best;
 }
 
