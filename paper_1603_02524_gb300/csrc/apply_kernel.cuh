@@ -17,6 +17,40 @@ __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 __device__ __forceinline__ double madd(double a, double b, double c) { return ::fma(a, b, c); }
 __device__ __forceinline__ float madd(float a, float b, float c) { return fmaf(a, b, c); }
 
+// 16-byte vector of T read through the read-only path (dfloat: two values per vector)
+template <typename T> struct AVec;
+template <> struct AVec<float> {
+  using V = float4;
+  static constexpr int W = 4;
+  __device__ static float get(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+};
+template <> struct AVec<double> {
+  using V = double2;
+  static constexpr int W = 2;
+  __device__ static double get(const double2& v, int k) { return k == 0 ? v.x : v.y; }
+};
+template <> struct AVec<dfloat> {
+  using V = float4;
+  static constexpr int W = 2;
+  __device__ static dfloat get(const float4& v, int k) { return k == 0 ? dfloat(v.x, v.y) : dfloat(v.z, v.w); }
+};
+template <typename T>
+__host__ __device__ constexpr int apad(int n) { return (n + AVec<T>::W - 1) / AVec<T>::W * AVec<T>::W; }
+
+// acc[0..N) += row[0..N) * x, row a 16-byte aligned, padded row of a global table
+template <typename T, int N>
+__device__ __forceinline__ void apply_axpy(T (&acc)[N], const T* row, T x) {
+  using A = AVec<T>;
+  const typename A::V* r = reinterpret_cast<const typename A::V*>(row);
+#pragma unroll
+  for (int c = 0; c < apad<T>(N) / A::W; ++c) {
+    const typename A::V w = __ldg(r + c);
+#pragma unroll
+    for (int k = 0; k < A::W; ++k)
+      if (c * A::W + k < N) acc[c * A::W + k] = madd(A::get(w, k), x, acc[c * A::W + k]);
+  }
+}
+
 // Allow `bytes` of dynamic shared memory for kernel `fn` (once per kernel).
 template <typename K>
 static bool set_smem(K fn, size_t bytes) {
@@ -104,9 +138,11 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
       T x[NP], y[NP];
 #pragma unroll
       for (int a = 0; a < NP; ++a) x[a] = sel[off + a * stride];
-      const T* L0 = at.L0[d] + (size_t)me[d] * NP * NP;
+      constexpr int PNP = apad<T>(NP);
+      const T* L0 = at.L0[d] + (size_t)me[d] * NP * PNP;
       if (__ldg(at.sym[d] + me[d])) {
-        // even-odd split of the centro-symmetric block (folded table layout)
+        // even-odd split of the centro-symmetric block (folded, transposed rows)
+        constexpr int PE = apad<T>(NE), PO = apad<T>(NO > 0 ? NO : 1);
         T xp[NE], xm[NO > 0 ? NO : 1];
 #pragma unroll
         for (int a = 0; a < H; ++a) {
@@ -114,38 +150,35 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
           xm[a] = x[a] - x[P - a];
         }
         if (NE > H) xp[NE - 1] = x[H];
-        const T* E = L0;
-        const T* O = L0 + NE * NE;
+        T ae[NE], ao[NO > 0 ? NO : 1];
+#pragma unroll
+        for (int i = 0; i < NE; ++i) ae[i] = T(0);
+#pragma unroll
+        for (int i = 0; i < NO; ++i) ao[i] = T(0);
+#pragma unroll
+        for (int a = 0; a < NE; ++a) apply_axpy<T, NE>(ae, L0 + a * PE, xp[a]);
+        if constexpr (NO > 0) {
+#pragma unroll
+          for (int a = 0; a < NO; ++a)
+            apply_axpy<T, NO>(reinterpret_cast<T(&)[NO]>(ao), L0 + NE * PE + a * PO, xm[a]);
+        }
 #pragma unroll
         for (int i = 0; i < H; ++i) {
-          T e = T(0), o = T(0);
-#pragma unroll
-          for (int a = 0; a < NE; ++a) e = madd(ldg(E + i * NE + a), xp[a], e);
-#pragma unroll
-          for (int a = 0; a < NO; ++a) o = madd(ldg(O + i * NO + a), xm[a], o);
-          y[i] = e + o;
-          y[P - i] = e - o;
+          y[i] = ae[i] + ao[i];
+          y[P - i] = ae[i] - ao[i];
         }
-        if (NE > H) {
-          T e = T(0);
-#pragma unroll
-          for (int a = 0; a < NE; ++a) e = madd(ldg(E + H * NE + a), xp[a], e);
-          y[H] = e;
-        }
+        if (NE > H) y[H] = ae[H];
       } else {
 #pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          T s = T(0);
+        for (int i = 0; i < NP; ++i) y[i] = T(0);
 #pragma unroll
-          for (int a = 0; a < NP; ++a) s = madd(ldg(L0 + i * NP + a), x[a], s);
-          y[i] = s;
-        }
+        for (int a = 0; a < NP; ++a) apply_axpy<T, NP>(y, L0 + a * PNP, x[a]);
       }
       // neighbour blocks L^-, L^+ (rank <= 3, already scaled by M_d^-1)
-      const T* c = at.cpl[d] + (size_t)me[d] * (2 * NP + 8);
+      const T* c = at.cpl[d] + (size_t)me[d] * (2 * PNP + 8);
       const long long estride = (d == 0) ? 1 : (d == 1 ? (long long)dm.ne[0] : (long long)dm.ne[0] * dm.ne[1]);
       const int ned = dm.ne[d];
-      if (ldg(c + 2 * NP + 2) != T(0)) {          // neighbour m-1 exists
+      if (ldg(c + 2 * PNP + 2) != T(0)) {          // neighbour m-1 exists
         long long en = (me[d] > 0) ? e - estride : e + (long long)(ned - 1) * estride;
         const TIO* un = u + en * S::NODES + off;
         T uP = T(0), dP = T(0);
@@ -155,11 +188,10 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
           dP = madd(ldg(at.DP + a), val, dP);
           if (a == P) uP = val;
         }
-#pragma unroll
-        for (int i = 0; i < NP; ++i) y[i] = madd(ldg(c + i), uP, y[i]);
-        y[0] += ldg(c + 2 * NP + 0) * dP - ldg(c + 2 * NP + 1) * uP;
+        apply_axpy<T, NP>(y, c, uP);
+        y[0] += ldg(c + 2 * PNP + 0) * dP - ldg(c + 2 * PNP + 1) * uP;
       }
-      if (ldg(c + 2 * NP + 5) != T(0)) {          // neighbour m+1 exists
+      if (ldg(c + 2 * PNP + 5) != T(0)) {          // neighbour m+1 exists
         long long en = (me[d] < ned - 1) ? e + estride : e - (long long)(ned - 1) * estride;
         const TIO* un = u + en * S::NODES + off;
         T u0 = T(0), d0 = T(0);
@@ -169,9 +201,8 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
           d0 = madd(ldg(at.D0 + a), val, d0);
           if (a == 0) u0 = val;
         }
-#pragma unroll
-        for (int i = 0; i < NP; ++i) y[i] = madd(ldg(c + NP + i), u0, y[i]);
-        y[P] = y[P] - (ldg(c + 2 * NP + 3) * d0 + ldg(c + 2 * NP + 4) * u0);
+        apply_axpy<T, NP>(y, c + PNP, u0);
+        y[P] = y[P] - (ldg(c + 2 * PNP + 3) * d0 + ldg(c + 2 * PNP + 4) * u0);
       }
 #pragma unroll
       for (int i = 0; i < NP; ++i) {

@@ -53,10 +53,11 @@ struct Axis1DHost {
 template <typename T>
 struct ApplyTables {
   // Per axis d and element index m along d:
-  const T* L0[3];     // [Ne_d][NP*NP]  M_d^-1 L^0 (row-scaled); even-odd folded when sym
+  // (accumulate form of apply_rowform: rows transposed and padded to 16 bytes)
+  const T* L0[3];     // [Ne_d][NP*pad(NP)] M_d^-1 L^0 (row-scaled); even-odd folded when sym
   const int* sym[3];  // [Ne_d]         1: M^-1 L^0 is centro-symmetric (folded form)
   const T* M[3];      // [Ne_d][NP]     diagonal mass M_d
-  const T* cpl[3];    // [Ne_d][2NP+8]  neighbour coupling, scaled by M_d^-1 (see setup)
+  const T* cpl[3];    // [Ne_d][2pad(NP)+8] neighbour coupling, scaled by M_d^-1 (see setup)
   const T* D0;        // D_{0,k}
   const T* DP;        // D_{P,k}
 };
@@ -66,6 +67,9 @@ struct ApplyAxisHost {
   std::vector<int> sym;
 };
 void apply_axis_tables(const Axis1DHost& a, ApplyAxisHost& t);
+// the same tables in the apply kernel's accumulate form, rows padded to W entries
+void apply_rowform(const ApplyAxisHost& t, int NP, int W, std::vector<double>& L0r,
+                   std::vector<double>& cplr);
 
 // One axis of a family of patches (EA, or FA with this axis normal/lateral).
 template <typename T>

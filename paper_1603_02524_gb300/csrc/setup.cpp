@@ -582,6 +582,42 @@ void apply_axis_tables(const Axis1DHost& a, ApplyAxisHost& t) {
   }
 }
 
+// The apply tables in the kernel's accumulate form: per element, the M^-1 L^0
+// block transposed (row a holds column a: general L^0[i][a] over i; even-odd:
+// the folded E then O blocks, transposed), each row padded to W entries (16
+// bytes of the device type), block stride NP * pad(NP); the coupling rows
+// c[0..NP) and c[NP..2NP) padded likewise, then the 8 scalars.
+void apply_rowform(const ApplyAxisHost& t, int NP, int W, std::vector<double>& L0r,
+                   std::vector<double>& cplr) {
+  auto pad = [W](int n) { return (n + W - 1) / W * W; };
+  const int H = NP / 2, NE = NP - H, NO = H;
+  const int PNP = pad(NP), PE = pad(NE), PO = pad(NO > 0 ? NO : 1);
+  const size_t LB = (size_t)NP * PNP, CB = 2 * (size_t)PNP + 8;
+  const int Ne = (int)t.sym.size();
+  L0r.assign((size_t)Ne * LB, 0.0);
+  cplr.assign((size_t)Ne * CB, 0.0);
+  for (int m = 0; m < Ne; ++m) {
+    const double* src = &t.L0[(size_t)m * NP * NP];
+    double* dst = &L0r[(size_t)m * LB];
+    if (t.sym[m]) {
+      for (int i = 0; i < NE; ++i)
+        for (int a = 0; a < NE; ++a) dst[(size_t)a * PE + i] = src[(size_t)i * NE + a];
+      for (int i = 0; i < NO; ++i)
+        for (int a = 0; a < NO; ++a) dst[(size_t)NE * PE + (size_t)a * PO + i] = src[(size_t)NE * NE + i * NO + a];
+    } else {
+      for (int i = 0; i < NP; ++i)
+        for (int a = 0; a < NP; ++a) dst[(size_t)a * PNP + i] = src[(size_t)i * NP + a];
+    }
+    const double* c = &t.cpl[(size_t)m * (2 * NP + 8)];
+    double* o = &cplr[(size_t)m * CB];
+    for (int i = 0; i < NP; ++i) {
+      o[i] = c[i];
+      o[PNP + i] = c[NP + i];
+    }
+    for (int j = 0; j < 8; ++j) o[2 * PNP + j] = c[2 * NP + j];
+  }
+}
+
 // Expand even-odd folded patch tables (sym = 1) into the general layout
 // (S node-major, W^T mode-major, symmetric modes first), for the tensor-core
 // line passes, which apply the full n x n tables.

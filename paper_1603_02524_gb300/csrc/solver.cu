@@ -1,9 +1,10 @@
 // C ABI, hierarchy construction, V-cycle (Algorithm 1) and inexact
 // multigrid-preconditioned CG (Algorithm 2) of Stiller, arXiv 1603.02524.
 //
-// Every per-iteration step is a kernel launched on the caller's stream; the
-// host only sequences launches and, once per CG iteration, reads the residual
-// norm to test convergence.
+// Every per-iteration step is a kernel launched on the caller's stream.  The
+// first solve of a hierarchy sequences its iterations from the host (reading the
+// residual norm once per iteration); later solves and batches replay CUDA graphs
+// whose iteration loop and convergence test run on the device.
 #include <array>
 #include <cmath>
 #include <cstdio>
@@ -135,10 +136,12 @@ ApplyTables<T> build_apply_tables(Hier& h, int l, std::vector<void*>& own) {
     int dd = d < dm.dim ? d : 0;
     ApplyAxisHost t;
     apply_axis_tables(ax[dd], t);
-    at.L0[d] = dev_upload<T>(own, t.L0);
+    std::vector<double> L0r, cplr;
+    apply_rowform(t, dm.NP, 16 / (int)sizeof(T), L0r, cplr);
+    at.L0[d] = dev_upload<T>(own, L0r);
     at.sym[d] = dev_upload_int(own, t.sym);
     at.M[d] = dev_upload<T>(own, ax[dd].M);
-    at.cpl[d] = dev_upload<T>(own, t.cpl);
+    at.cpl[d] = dev_upload<T>(own, cplr);
   }
   std::vector<double> D0(dm.NP), DP(dm.NP);
   for (int k = 0; k < dm.NP; ++k) {
