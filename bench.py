@@ -189,6 +189,8 @@ def oracle_baseline(w, opts, budget_s=30.0):
     except AttributeError:
         cores = os.cpu_count()
     return {"value": d.ndof / (t2 - t1), "unit": "DOF/s", "cores": cores, "kind": "oracle",
+            "threads": "NumPy: the BLAS products (tensordot, matmul) may use all the cores counted; "
+                       "the element-wise work runs on one",
             "sample": f"{'x'.join(map(str, ne))} elements at P={w.P} ({d.ndof} DOF), full MGCG solve to "
                       f"1e-10 ({len(hist) - 1} iterations, {t2 - t1:.1f} s; set-up {t1 - t0:.1f} s excluded)",
             "iterations": len(hist) - 1, "seconds": t2 - t1}
@@ -565,8 +567,13 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
         rel = float((um - u).abs().max() / u.abs().max())
         ms_o = time_kernel(lambda: native(hm), 5, stream, flush)
         t_o = statistics.mean(tm)
+        fl_o = 2.0 * hm.schwarz_sweep_fma(hm.L, fam)
+        pk_o = (FP64_PEAK_GFLOPS if prec == "fp64" else FP32_PEAK_GFLOPS) / 1e3
         entry = {"value": n / (t_o * 1e-3), "unit": "DOF/s", "ms_per_step": t_o, "iterations": itm,
-                 "status": rc, "max_rel_diff_between_solutions": rel, "patch_sweep_ms": ms_o}
+                 "status": rc, "max_rel_diff_between_solutions": rel, "patch_sweep_ms": ms_o,
+                 "smoother_gdof_s": n / (ms_o * 1e-3) / 1e9,
+                 "smoother_roofline_frac": fl_o / (ms_o * 1e-3) / 1e12 / pk_o,
+                 "smoother_peak": f"{'FP64' if prec == 'fp64' else 'FP32'} FMA, measured"}
         if other == "fp64_plain":
             line["fp64_plain"] = entry
             line["speedup_vs_fp64"] = t_o / line["ms_per_step"]
