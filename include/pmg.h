@@ -114,7 +114,7 @@ void pmg_options_default(pmg_options* opt);
 /*
  * Create a Cartesian grid description (Sec. 2.2).
  *   dim       2 or 3.
- *   P         polynomial order, a power of two, 1 <= P <= 16 in 3-D, <= 32 in 2-D
+ *   P         polynomial order, a power of two, 1 <= P <= 32
  *             (levels P_l = 2^l, Sec. 3.2).
  *   n_elem    elements per axis (n_elem[2] ignored in 2-D); each >= 1, and >= 2
  *             when periodic.

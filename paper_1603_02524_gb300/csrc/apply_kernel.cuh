@@ -71,6 +71,84 @@ static bool set_smem(K fn, size_t bytes) {
 // Each pass result is scaled by the diagonal masses of the two other axes and
 // accumulated in shared memory.
 // ---------------------------------------------------------------------------
+// y = M_d^-1 L_d u on one line of element e along axis d (nodes off + a * stride of
+// the element, values x): the element's own block L^0 (even-odd form when the block
+// is centro-symmetric), plus the neighbour blocks L^-, L^+ from the adjacent lines
+// in global u.
+template <typename T, int NP, int NODES, typename TIO>
+__device__ __forceinline__ void apply_line(const LevelDims& dm, const ApplyTables<T>& at,
+                                           const TIO* __restrict__ u, long long e, const int (&me)[3],
+                                           int d, int off, int stride, const T (&x)[NP], T (&y)[NP]) {
+  constexpr int P = NP - 1;
+  constexpr int H = NP / 2, NE = NP - H, NO = H;
+  constexpr int PNP = apad<T>(NP);
+  const T* L0 = at.L0[d] + (size_t)me[d] * NP * PNP;
+  if (__ldg(at.sym[d] + me[d])) {
+    // even-odd split of the centro-symmetric block (folded, transposed rows)
+    constexpr int PE = apad<T>(NE), PO = apad<T>(NO > 0 ? NO : 1);
+    T xp[NE], xm[NO > 0 ? NO : 1];
+#pragma unroll
+    for (int a = 0; a < H; ++a) {
+      xp[a] = x[a] + x[P - a];
+      xm[a] = x[a] - x[P - a];
+    }
+    if (NE > H) xp[NE - 1] = x[H];
+    T ae[NE], ao[NO > 0 ? NO : 1];
+#pragma unroll
+    for (int i = 0; i < NE; ++i) ae[i] = T(0);
+#pragma unroll
+    for (int i = 0; i < NO; ++i) ao[i] = T(0);
+#pragma unroll
+    for (int a = 0; a < NE; ++a) apply_axpy<T, NE>(ae, L0 + a * PE, xp[a]);
+    if constexpr (NO > 0) {
+#pragma unroll
+      for (int a = 0; a < NO; ++a)
+        apply_axpy<T, NO>(reinterpret_cast<T(&)[NO]>(ao), L0 + NE * PE + a * PO, xm[a]);
+    }
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      y[i] = ae[i] + ao[i];
+      y[P - i] = ae[i] - ao[i];
+    }
+    if (NE > H) y[H] = ae[H];
+  } else {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) y[i] = T(0);
+#pragma unroll
+    for (int a = 0; a < NP; ++a) apply_axpy<T, NP>(y, L0 + a * PNP, x[a]);
+  }
+  // neighbour blocks L^-, L^+ (rank <= 3, already scaled by M_d^-1)
+  const T* c = at.cpl[d] + (size_t)me[d] * (2 * PNP + 8);
+  const long long estride = (d == 0) ? 1 : (d == 1 ? (long long)dm.ne[0] : (long long)dm.ne[0] * dm.ne[1]);
+  const int ned = dm.ne[d];
+  if (ldg(c + 2 * PNP + 2) != T(0)) {          // neighbour m-1 exists
+    long long en = (me[d] > 0) ? e - estride : e + (long long)(ned - 1) * estride;
+    const TIO* un = u + en * NODES + off;
+    T uP = T(0), dP = T(0);
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      T val = T(__ldg(un + a * stride));
+      dP = madd(ldg(at.DP + a), val, dP);
+      if (a == P) uP = val;
+    }
+    apply_axpy<T, NP>(y, c, uP);
+    y[0] += ldg(c + 2 * PNP + 0) * dP - ldg(c + 2 * PNP + 1) * uP;
+  }
+  if (ldg(c + 2 * PNP + 5) != T(0)) {          // neighbour m+1 exists
+    long long en = (me[d] < ned - 1) ? e + estride : e - (long long)(ned - 1) * estride;
+    const TIO* un = u + en * NODES + off;
+    T u0 = T(0), d0 = T(0);
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      T val = T(__ldg(un + a * stride));
+      d0 = madd(ldg(at.D0 + a), val, d0);
+      if (a == 0) u0 = val;
+    }
+    apply_axpy<T, NP>(y, c + PNP, u0);
+    y[P] = y[P] - (ldg(c + 2 * PNP + 3) * d0 + ldg(c + 2 * PNP + 4) * u0);
+  }
+}
+
 template <int DIM, int NP>
 struct ApplyShape {
   static constexpr int LINES = (DIM == 3) ? NP * NP : NP;
@@ -138,72 +216,7 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
       T x[NP], y[NP];
 #pragma unroll
       for (int a = 0; a < NP; ++a) x[a] = sel[off + a * stride];
-      constexpr int PNP = apad<T>(NP);
-      const T* L0 = at.L0[d] + (size_t)me[d] * NP * PNP;
-      if (__ldg(at.sym[d] + me[d])) {
-        // even-odd split of the centro-symmetric block (folded, transposed rows)
-        constexpr int PE = apad<T>(NE), PO = apad<T>(NO > 0 ? NO : 1);
-        T xp[NE], xm[NO > 0 ? NO : 1];
-#pragma unroll
-        for (int a = 0; a < H; ++a) {
-          xp[a] = x[a] + x[P - a];
-          xm[a] = x[a] - x[P - a];
-        }
-        if (NE > H) xp[NE - 1] = x[H];
-        T ae[NE], ao[NO > 0 ? NO : 1];
-#pragma unroll
-        for (int i = 0; i < NE; ++i) ae[i] = T(0);
-#pragma unroll
-        for (int i = 0; i < NO; ++i) ao[i] = T(0);
-#pragma unroll
-        for (int a = 0; a < NE; ++a) apply_axpy<T, NE>(ae, L0 + a * PE, xp[a]);
-        if constexpr (NO > 0) {
-#pragma unroll
-          for (int a = 0; a < NO; ++a)
-            apply_axpy<T, NO>(reinterpret_cast<T(&)[NO]>(ao), L0 + NE * PE + a * PO, xm[a]);
-        }
-#pragma unroll
-        for (int i = 0; i < H; ++i) {
-          y[i] = ae[i] + ao[i];
-          y[P - i] = ae[i] - ao[i];
-        }
-        if (NE > H) y[H] = ae[H];
-      } else {
-#pragma unroll
-        for (int i = 0; i < NP; ++i) y[i] = T(0);
-#pragma unroll
-        for (int a = 0; a < NP; ++a) apply_axpy<T, NP>(y, L0 + a * PNP, x[a]);
-      }
-      // neighbour blocks L^-, L^+ (rank <= 3, already scaled by M_d^-1)
-      const T* c = at.cpl[d] + (size_t)me[d] * (2 * PNP + 8);
-      const long long estride = (d == 0) ? 1 : (d == 1 ? (long long)dm.ne[0] : (long long)dm.ne[0] * dm.ne[1]);
-      const int ned = dm.ne[d];
-      if (ldg(c + 2 * PNP + 2) != T(0)) {          // neighbour m-1 exists
-        long long en = (me[d] > 0) ? e - estride : e + (long long)(ned - 1) * estride;
-        const TIO* un = u + en * S::NODES + off;
-        T uP = T(0), dP = T(0);
-#pragma unroll
-        for (int a = 0; a < NP; ++a) {
-          T val = T(__ldg(un + a * stride));
-          dP = madd(ldg(at.DP + a), val, dP);
-          if (a == P) uP = val;
-        }
-        apply_axpy<T, NP>(y, c, uP);
-        y[0] += ldg(c + 2 * PNP + 0) * dP - ldg(c + 2 * PNP + 1) * uP;
-      }
-      if (ldg(c + 2 * PNP + 5) != T(0)) {          // neighbour m+1 exists
-        long long en = (me[d] < ned - 1) ? e + estride : e - (long long)(ned - 1) * estride;
-        const TIO* un = u + en * S::NODES + off;
-        T u0 = T(0), d0 = T(0);
-#pragma unroll
-        for (int a = 0; a < NP; ++a) {
-          T val = T(__ldg(un + a * stride));
-          d0 = madd(ldg(at.D0 + a), val, d0);
-          if (a == 0) u0 = val;
-        }
-        apply_axpy<T, NP>(y, c + PNP, u0);
-        y[P] = y[P] - (ldg(c + 2 * PNP + 3) * d0 + ldg(c + 2 * PNP + 4) * u0);
-      }
+      apply_line<T, NP, S::NODES, TIO>(dm, at, u, e, me, d, off, stride, x, y);
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
         if (d == 0) ael[off + i * stride] = y[i];
@@ -229,6 +242,64 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
     const T val = m * acc[t];
     v[g] = RESIDUAL ? TIO(T(f[g]) - val) : TIO(val);
   }
+}
+
+// 3-D elements too large to stage in shared memory (P = 32: 33^3 nodes): one
+// launch per axis d and one thread per (element, line).  The partial sums over
+// the axes are kept in v between the launches (the same additions, in the same
+// order, as the staged kernel's accumulator); the launch of the last axis applies
+// the masses and forms v = A u or f - A u.
+template <typename T, int NP, bool RESIDUAL, typename TIO>
+__global__ void __launch_bounds__(128)
+apply_axis_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u,
+                  const TIO* __restrict__ f, TIO* __restrict__ v, int d) {
+  constexpr int LINES = NP * NP, NODES = NP * NP * NP;
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= dm.nelem * LINES) return;
+  const long long e = gid / LINES;
+  const int line = (int)(gid - e * LINES);
+  const int me[3] = {(int)(e % dm.ne[0]), (int)((e / dm.ne[0]) % dm.ne[1]),
+                     (int)(e / ((long long)dm.ne[0] * dm.ne[1]))};
+  int off, stride;
+  if (d == 0) { off = line * NP; stride = 1; }
+  else if (d == 1) { off = (line / NP) * NP * NP + line % NP; stride = NP; }
+  else { off = line; stride = NP * NP; }
+  const TIO* ue = u + e * NODES;
+  TIO* ve = v + e * NODES;
+  T x[NP], y[NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) x[a] = T(ue[off + a * stride]);
+  apply_line<T, NP, NODES, TIO>(dm, at, u, e, me, d, off, stride, x, y);
+  if (d == 0) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) ve[off + i * stride] = TIO(y[i]);
+  } else if (d == 1) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) ve[off + i * stride] = TIO(T(ve[off + i * stride]) + y[i]);
+  } else {
+#pragma unroll 1
+    for (int i = 0; i < NP; ++i) {
+      const int nd = off + i * stride;
+      const int ii = nd % NP, jj = (nd / NP) % NP, kk = nd / (NP * NP);
+      T m = ldg(at.M[0] + (size_t)me[0] * NP + ii) * ldg(at.M[1] + (size_t)me[1] * NP + jj);
+      m = m * ldg(at.M[2] + (size_t)me[2] * NP + kk);
+      const T val = m * (T(ve[nd]) + y[i]);
+      ve[nd] = RESIDUAL ? TIO(T(f[e * NODES + nd]) - val) : TIO(val);
+    }
+  }
+}
+
+template <typename T, int NP, typename TIO>
+static int apply_dispatch_axes(const LevelDims& dm, const ApplyTables<T>& at, const TIO* u, const TIO* f,
+                               TIO* v, cudaStream_t s) {
+  const long long threads = dm.nelem * NP * NP;
+  const long long blocks = (threads + 127) / 128;
+  for (int d = 0; d < 3; ++d) {
+    count_launch();
+    if (f) apply_axis_kernel<T, NP, true, TIO><<<(unsigned)blocks, 128, 0, s>>>(dm, at, u, f, v, d);
+    else apply_axis_kernel<T, NP, false, TIO><<<(unsigned)blocks, 128, 0, s>>>(dm, at, u, f, v, d);
+  }
+  return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
 }
 
 template <typename T, int DIM, int NP, typename TIO = T>

@@ -12,6 +12,7 @@ int fdm_dispatch_d3(const LevelDims& dm, const FdmFamily<double>& fam, const dou
   C(3, 3, 3) C(5, 5, 5) C(7, 7, 7) C(9, 9, 9) C(13, 13, 13) C(17, 17, 17) C(23, 23, 23)
   C(4, 3, 3) C(4, 5, 5) C(8, 5, 5) C(8, 7, 7) C(8, 9, 9) C(16, 9, 9) C(16, 13, 13)
   C(32, 17, 17) C(32, 23, 23)
+  C(33, 33, 33) C(43, 43, 43) C(64, 33, 33) C(64, 43, 43)    // P = 32: patch buffers in global scratch
 #undef C
   return PMG_EINVAL;
 }

@@ -617,6 +617,94 @@ fdm_kernel_pipe(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __re
   }
 }
 
+// ---------------------------------------------------------------------------
+// Patches too large for shared memory (3-D, P = 32: n = 43, and the face patches
+// 64 x 43 x 43): persistent CTAs keep their patch buffer in a global scratch
+// array (one buffer per CTA, reused patch after patch; it stays in L2 while the
+// CTA works on it) and only the offsets, tables and eigenvalues in shared memory.
+// ---------------------------------------------------------------------------
+template <typename T, int NA, int NB, int NC>
+constexpr size_t fdm_gbuf_smem_bytes() {
+  return sizeof(long long) * ((NA + NB + NC + 1) / 2 * 2 + (NB * NC + 1) / 2 * 2) +
+         sizeof(T) * (2 * (size_t)(table_floats<T, false>(NA) + table_floats<T, false>(NB) +
+                                   table_floats<T, false>(NC)) + NA + NB + NC);
+}
+
+template <typename T, int NA, int NB, int NC>
+__global__ void __launch_bounds__(256)
+fdm_kernel_gbuf(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restrict__ u) {
+  constexpr int NN = NA * NB * NC;
+  extern __shared__ __align__(16) unsigned char fdm_smem[];
+  long long* off = reinterpret_cast<long long*>(fdm_smem);
+  long long* rowoff = off + (NA + NB + NC + 1) / 2 * 2;
+  T* tb = reinterpret_cast<T*>(rowoff + (NB * NC + 1) / 2 * 2);
+  T* const Sq[3] = {tb, tb + 2 * table_floats<T, false>(NA),
+                    tb + 2 * (table_floats<T, false>(NA) + table_floats<T, false>(NB))};
+  T* const Wq[3] = {Sq[0] + table_floats<T, false>(NA), Sq[1] + table_floats<T, false>(NB),
+                    Sq[2] + table_floats<T, false>(NC)};
+  T* la = Sq[2] + 2 * table_floats<T, false>(NC);
+  T* lb = la + NA;
+  T* lc = lb + NB;
+  T* buf = fam.scratch + (long long)blockIdx.x * fam.scratch_stride;
+  const int ca = fam.ax[0].count, cb = fam.ax[1].count;
+  const int nq[3] = {NA, NB, NC};
+  T* lq[3] = {la, lb, lc};
+  long long* offq[3] = {off, off + NA, off + NA + NB};
+  const long long nodes_el = (long long)dm.NP * dm.NP * dm.NPz;
+  const long long estride[3] = {nodes_el, nodes_el * dm.ne[0], nodes_el * dm.ne[0] * dm.ne[1]};
+  const long long nstride[3] = {1, dm.NP, (long long)dm.NP * dm.NP};
+  for (int pid = blockIdx.x; pid < fam.count_total; pid += gridDim.x) {
+    const int pidx[3] = {pid % ca, (pid / ca) % cb, pid / (ca * cb)};
+    bool sym[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const FdmAxis<T>& ax = fam.ax[q];
+      const int n = nq[q];
+      const size_t p = pidx[q];
+      sym[q] = ax.sym[p] != 0;
+      if (q == 0) {
+        load_table<T, NA>(Sq[0], ax.S + p * n * n, sym[0]);
+        load_table<T, NA>(Wq[0], ax.W + p * n * n, sym[0]);
+      } else if (q == 1) {
+        load_table<T, NB>(Sq[1], ax.S + p * n * n, sym[1]);
+        load_table<T, NB>(Wq[1], ax.W + p * n * n, sym[1]);
+      } else {
+        load_table<T, NC>(Sq[2], ax.S + p * n * n, sym[2]);
+        load_table<T, NC>(Wq[2], ax.W + p * n * n, sym[2]);
+      }
+      for (int a = threadIdx.x; a < n; a += blockDim.x) {
+        lq[q][a] = ax.lam[p * n + a];
+        const int ph = ax.phys;
+        const int npp = (ph == 2) ? dm.NPz : dm.NP;
+        int G = ax.start0 + (int)p * npp + a;
+        long long o;
+        if (ax.periodic) {
+          G %= ax.N;
+          if (G < 0) G += ax.N;
+          o = (long long)(G / npp) * estride[ph] + (G % npp) * nstride[ph];
+        } else if (G < 0 || G >= ax.N) {
+          o = kInvalidOffset;
+        } else {
+          o = (long long)(G / npp) * estride[ph] + (G % npp) * nstride[ph];
+        }
+        offq[q][a] = o;
+      }
+    }
+    __syncthreads();
+    for (int rr = threadIdx.x; rr < NB * NC; rr += blockDim.x)
+      rowoff[rr] = off[NA + rr % NB] + off[NA + NB + rr / NB];
+    __syncthreads();
+    for (int t = threadIdx.x; t < NN; t += blockDim.x) {
+      const int row = t / NA, a = t - row * NA;
+      const long long o = off[a] + rowoff[row];
+      buf[t] = o >= 0 ? r[o] : T(0);
+    }
+    __syncthreads();
+    patch_compute<T, NA, NB, NC, false>(buf, Sq, Wq, la, lb, lc, sym, off, rowoff, u);
+    __syncthreads();
+  }
+}
+
 template <typename T, int NA, int NB, int NC, bool TC>
 constexpr size_t fdm_smem_bytes() {
   return sizeof(long long) * ((NA + NB + NC + 1) / 2 * 2 + (NB * NC + 1) / 2 * 2) +
@@ -660,6 +748,27 @@ int fdm_launch(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, c
     fdm_kernel_pipe<T, NA, NB, NC><<<(unsigned)grid, threads, smem2, s>>>(dm, fam, r, u);
     return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
   }
+  if constexpr (fdm_smem_bytes<T, NA, NB, NC, TC>() > 227 * 1024) {
+    static_assert(!TC, "tensor-core passes need the patch in shared memory");
+    constexpr size_t smem_g = fdm_gbuf_smem_bytes<T, NA, NB, NC>();
+    static_assert(smem_g <= 227 * 1024, "patch tables do not fit in shared memory");
+    if (!fam.scratch || fam.scratch_ctas <= 0 || fam.scratch_stride < (long long)NA * NB * NC)
+      return PMG_EINVAL;
+    static bool attr_g = false;
+    if (!attr_g && smem_g > 48 * 1024) {
+      if (cudaFuncSetAttribute(fdm_kernel_gbuf<T, NA, NB, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_g) != cudaSuccess)
+        return PMG_ECUDA;
+    }
+    attr_g = true;
+    if (fam.count_total <= 0) return PMG_OK;
+    int threads = (fam.threads >= 32 && fam.threads % 32 == 0) ? fam.threads : 256;
+    if (threads > 256) threads = 256;
+    const int grid = fam.count_total < fam.scratch_ctas ? fam.count_total : fam.scratch_ctas;
+    count_launch();
+    fdm_kernel_gbuf<T, NA, NB, NC><<<grid, threads, smem_g, s>>>(dm, fam, r, u);
+    return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
+  } else {
   constexpr size_t smem = fdm_smem_bytes<T, NA, NB, NC, TC>();
   static_assert(smem <= 227 * 1024, "patch does not fit in shared memory");
   static bool attr_done = false;
@@ -676,6 +785,7 @@ int fdm_launch(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, c
   count_launch();
   fdm_kernel<T, NA, NB, NC, TC><<<fam.count_total, threads, smem, s>>>(dm, fam, r, u);
   return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
+  }
 }
 
 }  // namespace pmg

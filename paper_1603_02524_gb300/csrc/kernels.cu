@@ -20,6 +20,7 @@ int launch_apply(const LevelDims& dm, const ApplyTables<T>& at, const T* u, cons
   if (dm.dim == DIMV && dm.NP == NPV) return apply_dispatch<T, DIMV, NPV>(dm, at, u, f, v, s);
   PMG_APPLY_CASE(3, 2) PMG_APPLY_CASE(3, 3) PMG_APPLY_CASE(3, 5) PMG_APPLY_CASE(3, 9)
   PMG_APPLY_CASE(3, 17)
+  if (dm.dim == 3 && dm.NP == 33) return apply_dispatch_axes<T, 33, T>(dm, at, u, f, v, s);
   PMG_APPLY_CASE(2, 2) PMG_APPLY_CASE(2, 3) PMG_APPLY_CASE(2, 5) PMG_APPLY_CASE(2, 9)
   PMG_APPLY_CASE(2, 17) PMG_APPLY_CASE(2, 33)
 #undef PMG_APPLY_CASE
@@ -117,6 +118,89 @@ transfer_kernel(long long nelem, const T* __restrict__ J, const T* __restrict__ 
   }
 }
 
+// 3-D transfers between P = 32 and P = 16 (33 and 17 nodes per axis): the
+// three element-sized buffers of transfer_kernel do not fit shared memory, so the
+// passes share one buffer of 17 x 33 x 33 entries: the first pass reads global
+// memory, the middle pass works in place line by line (a thread holds its whole
+// line in registers before it writes it), the last pass writes global memory.
+template <typename T, bool PROLONG>
+__global__ void __launch_bounds__(256)
+transfer_big_kernel(long long nelem, const T* __restrict__ J, const T* __restrict__ in,
+                    T* __restrict__ out) {
+  constexpr int F = 33, C = 17;
+  extern __shared__ __align__(16) unsigned char trb_smem[];
+  T* sJ = reinterpret_cast<T*>(trb_smem);          // J[f][c]
+  T* b = sJ + F * C;                                // [C][F][F]
+  const long long e = blockIdx.x;
+  for (int t = threadIdx.x; t < F * C; t += blockDim.x) sJ[t] = J[t];
+  __syncthreads();
+  if (!PROLONG) {
+    const T* ie = in + e * (F * F * F);
+    for (int t = threadIdx.x; t < C * F * F; t += blockDim.x) {   // z: F -> C
+      const int oz = t / (F * F), rem = t - oz * F * F;
+      T s = T(0);
+#pragma unroll 1
+      for (int k = 0; k < F; ++k) s = fma(sJ[k * C + oz], ie[k * F * F + rem], s);
+      b[t] = s;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < C * F; l += blockDim.x) {       // y: F -> C, in place
+      const int oz = l / F, i = l - oz * F;
+      T v[F];
+#pragma unroll
+      for (int j = 0; j < F; ++j) v[j] = b[(oz * F + j) * F + i];
+#pragma unroll
+      for (int oj = 0; oj < C; ++oj) {
+        T s = T(0);
+#pragma unroll
+        for (int j = 0; j < F; ++j) s = fma(sJ[j * C + oj], v[j], s);
+        b[(oz * F + oj) * F + i] = s;
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < C * C * C; t += blockDim.x) {   // x: F -> C, to global
+      const int ox = t % C, oj = (t / C) % C, oz = t / (C * C);
+      const T* row = b + (oz * F + oj) * F;
+      T s = T(0);
+#pragma unroll
+      for (int i = 0; i < F; ++i) s = fma(sJ[i * C + ox], row[i], s);
+      out[e * (C * C * C) + t] = s;
+    }
+  } else {
+    const T* ie = in + e * (C * C * C);
+    for (int t = threadIdx.x; t < C * C * F; t += blockDim.x) {   // x: C -> F
+      const int xo = t % F, jc = (t / F) % C, kc = t / (F * C);
+      const T* row = ie + (kc * C + jc) * C;
+      T s = T(0);
+#pragma unroll
+      for (int ic = 0; ic < C; ++ic) s = fma(sJ[xo * C + ic], row[ic], s);
+      b[(kc * F + jc) * F + xo] = s;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < C * F; l += blockDim.x) {       // y: C -> F, in place
+      const int kc = l / F, xo = l - kc * F;
+      T v[C];
+#pragma unroll
+      for (int jc = 0; jc < C; ++jc) v[jc] = b[(kc * F + jc) * F + xo];
+#pragma unroll
+      for (int yo = 0; yo < F; ++yo) {
+        T s = T(0);
+#pragma unroll
+        for (int jc = 0; jc < C; ++jc) s = fma(sJ[yo * C + jc], v[jc], s);
+        b[(kc * F + yo) * F + xo] = s;
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < F * F * F; t += blockDim.x) {   // z: C -> F, add to global
+      const int xy = t % (F * F), zo = t / (F * F);
+      T s = T(0);
+#pragma unroll
+      for (int kc = 0; kc < C; ++kc) s = fma(sJ[zo * C + kc], b[kc * F * F + xy], s);
+      out[e * (F * F * F) + t] += s;
+    }
+  }
+}
+
 template <typename T, bool PROLONG>
 static int transfer_launch(const LevelDims& fine, const LevelDims& coarse, const T* J, const T* in,
                            T* out, cudaStream_t s) {
@@ -134,6 +218,12 @@ static int transfer_launch(const LevelDims& fine, const LevelDims& coarse, const
   PMG_TR_CASE(2, 3, 2) PMG_TR_CASE(2, 5, 3) PMG_TR_CASE(2, 9, 5) PMG_TR_CASE(2, 17, 9)
   PMG_TR_CASE(2, 33, 17)
 #undef PMG_TR_CASE
+  if (fine.dim == 3 && fine.NP == 33 && coarse.NP == 17) {
+    const size_t smem = sizeof(T) * (33 * 17 + 17 * 33 * 33);
+    if (!set_smem(transfer_big_kernel<T, PROLONG>, smem)) return PMG_ECUDA;
+    count_launch(); transfer_big_kernel<T, PROLONG><<<blocks, 256, smem, s>>>(fine.nelem, J, in, out);
+    return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
+  }
   return PMG_EINVAL;
 }
 

@@ -97,6 +97,11 @@ struct FdmFamily {
   int tc = 0;          // fp32 only: 1 = line passes on the tensor cores (tables unfolded)
   int threads = 0;     // CTA size chosen by the autotuner (0: the kernel's default)
   int variant = -1;    // fp32: 0 one patch per CTA, 1 pipelined persistent CTAs, -1 default
+  // patches too large for shared memory (3-D, P = 32): the patch buffers of the
+  // persistent CTAs in global memory, scratch_ctas buffers of scratch_stride entries
+  T* scratch = nullptr;
+  int scratch_ctas = 0;
+  long long scratch_stride = 0;
 };
 
 struct LevelDims {

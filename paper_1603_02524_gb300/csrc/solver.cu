@@ -153,6 +153,27 @@ ApplyTables<T> build_apply_tables(Hier& h, int l, std::vector<void*>& own) {
   return at;
 }
 
+// Shared memory the one-patch-per-CTA kernel needs for a patch of n0 x n1 x n2
+// (as fdm_smem_bytes); beyond 227 KB the patch buffers go to global scratch.
+template <typename T>
+size_t patch_smem_bytes(int n0, int n1, int n2) {
+  const int W = 16 / (int)sizeof(T);
+  auto pad = [W](long long n) { return (n + W - 1) / W * W; };
+  const long long NN = (long long)n0 * n1 * n2;
+  const long long tf = (long long)n0 * pad(n0) + (long long)n1 * pad(n1) + (long long)n2 * pad(n2);
+  return sizeof(long long) * (size_t)((n0 + n1 + n2 + 1) / 2 * 2 + ((long long)n1 * n2 + 1) / 2 * 2) +
+         sizeof(T) * (size_t)(pad(NN) + 2 * tf + n0 + n1 + n2);
+}
+
+template <typename T>
+void attach_scratch(Hier& h, FdmFamily<T>& fam, std::vector<void*>& own) {
+  const int n0 = fam.ax[0].n, n1 = fam.ax[1].n, n2 = fam.ax[2].n;
+  if (patch_smem_bytes<T>(n0, n1, n2) <= 227 * 1024) return;
+  fam.scratch_ctas = 2 * h.nsm;
+  fam.scratch_stride = ((long long)n0 * n1 * n2 + 31) / 32 * 32;
+  fam.scratch = dev_alloc<T>(own, (size_t)fam.scratch_ctas * fam.scratch_stride);
+}
+
 template <typename T>
 void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTables>& ec,
                      const std::vector<AxisTables>& fc) {
@@ -185,6 +206,7 @@ void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTab
         fam.ax[q] = trivial_axis<T>(own);
       }
     }
+    attach_scratch<T>(h, fam, own);
     dev.ea = fam;
   } else {
     for (int nrm = 0; nrm < dm.dim; ++nrm) {
@@ -200,6 +222,7 @@ void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTab
         ++q;
       }
       for (; q < 3; ++q) fam.ax[q] = trivial_axis<T>(own);
+      attach_scratch<T>(h, fam, own);
       dev.fa[nrm] = fam;
     }
   }
@@ -730,7 +753,7 @@ int pmg_grid_create(int dim, int P, const int n_elem[3], const double* const spa
   if (!out || !n_elem || !spacing) return PMG_EINVAL;
   *out = nullptr;
   if (dim != 2 && dim != 3) return PMG_EINVAL;
-  if (P < 1 || (P & (P - 1)) != 0 || P > (dim == 3 ? 16 : 32)) return PMG_EINVAL;
+  if (P < 1 || (P & (P - 1)) != 0 || P > 32) return PMG_EINVAL;
   if (!(mu_star > -1.0)) return PMG_EINVAL;
   try {
     Grid* g = new Grid();

@@ -46,7 +46,7 @@ def test_grid_argument_checks(lib):
     with pytest.raises(PmgError):
         Grid(3, 3, (2, 2, 2), sp, periodic=False)        # P not a power of two
     with pytest.raises(PmgError):
-        Grid(3, 32, (2, 2, 2), sp, periodic=False)       # P = 32 only in 2-D
+        Grid(3, 64, (2, 2, 2), sp, periodic=False)       # P <= 32
     with pytest.raises(PmgError):
         Grid(4, 2, (2, 2, 2), sp, periodic=False)
     with pytest.raises(PmgError):
@@ -54,6 +54,7 @@ def test_grid_argument_checks(lib):
     with pytest.raises(PmgError):
         Grid(2, 2, (2, 2), [[0.5, -0.5], [0.5, 0.5]], periodic=False)
     Grid(2, 32, (2, 2), [[0.5, 0.5]] * 2, periodic=True).close()
+    Grid(3, 32, (2, 2, 2), sp, periodic=False).close()
 
 
 def test_node_coordinates_match_oracle(lib):
