@@ -71,7 +71,7 @@ DTYPE = {("fp64", "fp64"): "f64", ("mixed", "fp64"): "f64+f32", ("mixed_tc", "fp
 VARIANTS = {"fp64_plain": ("fp64", "fp64"), "mixed": ("mixed", "fp64"), "mixed_tc": ("mixed_tc", "fp64"),
             "mixed_df": ("mixed", "df")}
 BATCH_OPTS = dict(smoother="FA", overlap="l", variable_v=True)
-BATCH_NAME = "batched_64grids_4rhs_3d_P4-16_aspect1-16"
+BATCH_NAME = "batched_64grids_4rhs_3d_P4-32_aspect1-16"
 
 
 def workload(name):
@@ -233,7 +233,7 @@ def run_reference(args):
 
 
 def main_batch(args):
-    """Workload c5: 64 independent 3-D grids (n^3 elements, n in {8,12,16,24}; P in {4,8,16};
+    """Workload c5: 64 independent 3-D grids (n^3 elements, n in {8,12,16,24}; P in {4,8,16,32};
     element aspect ratios 1..16), 4 seeded Gaussian right-hand sides each, all solved to
     1e-10 by one batched call (one CUDA graph launch); value = all solves' DOF / time."""
     import torch

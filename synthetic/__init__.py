@@ -178,11 +178,11 @@ def source_values(w: Workload, coords_1d: list) -> np.ndarray:
 
 
 BATCH_SIDES = (8, 12, 16, 24)      # elements per axis of a batched grid
-BATCH_ORDERS = (4, 8, 16)          # P = 32 in 3-D is outside the library's 3-D range
+BATCH_ORDERS = (4, 8, 16, 32)
 
 
 def config5(n_grids: int = 64, n_rhs: int = 4, budget_dof: int = 512_000_000,
-            grid_cap_dof: int = 64_000_000, seed: int = 0) -> list:
+            grid_cap_dof: int = 80_000_000, seed: int = 0) -> list:
     """Batched solves: n_grids independent 3-D Dirichlet grids on (0,1) x (0,ry) x (0,rz)
     with n^3 elements, n drawn from BATCH_SIDES and P from BATCH_ORDERS; widths
     hx = 1/n, hy = ry/n, hz = rz/n with ry, rz log-uniform in [1/4, 4], so element

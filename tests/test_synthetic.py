@@ -15,7 +15,7 @@ def test_batch_draws_respect_budget_and_ranges():
         n = w.n_elem[0]
         assert w.n_elem == (n, n, n) and n in syn.BATCH_SIDES
         assert w.P in syn.BATCH_ORDERS and w.dim == 3 and not w.periodic
-        assert w.ndof * w.extra["n_rhs"] <= 64_000_000
+        assert w.ndof * w.extra["n_rhs"] <= 80_000_000
         widths = [s[0] for s in w.spacing]
         assert all(len(set(s)) == 1 and len(s) == n for s in w.spacing)
         ratio = max(widths) / min(widths)
