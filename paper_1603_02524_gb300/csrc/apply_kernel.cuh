@@ -5,6 +5,8 @@
 // the tensor form of the discrete problem (Sec. 2.2, reading C1 in 3-D).
 #pragma once
 
+#include <type_traits>
+
 #include "pmg_internal.h"
 
 namespace pmg {
@@ -201,7 +203,11 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
   T* sel = su + el * S::NODES;
   T* ael = acc + el * S::NODES;
   constexpr int H = NP / 2, NE = NP - H, NO = H;
-#pragma unroll 1
+  // axes unrolled (line offsets and strides become compile-time constants) for the
+  // fp32 and FP64 kernels, except FP64 at P = 16, whose register cap would then spill;
+  // the double-float kernel was measured faster without (instruction-cache pressure)
+  constexpr int UNR = (std::is_same<T, dfloat>::value || (sizeof(T) == 8 && NP == 17)) ? 1 : DIM;
+#pragma unroll UNR
   for (int d = 0; d < DIM; ++d) {
     if (active) {
       int off, stride;

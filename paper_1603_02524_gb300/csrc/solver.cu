@@ -169,8 +169,14 @@ template <typename T>
 void attach_scratch(Hier& h, FdmFamily<T>& fam, std::vector<void*>& own) {
   const int n0 = fam.ax[0].n, n1 = fam.ax[1].n, n2 = fam.ax[2].n;
   if (patch_smem_bytes<T>(n0, n1, n2) <= 227 * 1024) return;
-  fam.scratch_ctas = 2 * h.nsm;
   fam.scratch_stride = ((long long)n0 * n1 * n2 + 31) / 32 * 32;
+  // two CTAs per SM, fewer (down to one per SM) when their buffers would not stay
+  // within ~96 MB of the 126 MB L2
+  const long long per = fam.scratch_stride * (long long)sizeof(T);
+  long long ctas = (96LL << 20) / per;
+  if (ctas > 2 * h.nsm) ctas = 2 * h.nsm;
+  if (ctas < h.nsm) ctas = h.nsm;
+  fam.scratch_ctas = (int)ctas;
   fam.scratch = dev_alloc<T>(own, (size_t)fam.scratch_ctas * fam.scratch_stride);
 }
 
