@@ -51,7 +51,7 @@ def parse():
                     choices=["c1", "c2", "c2ldg", "c2x32", "c3", "c3s", "c4", "c5"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed_tc"],
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed_tc", "mixed_tf32"],
                     help="arithmetic of the timed solve's V-cycle (the outer CG is always FP64); "
                          "default fp64, mixed for the batched workload c5")
     ap.add_argument("--autotune", action="store_true",
@@ -66,10 +66,12 @@ def parse():
 
 # arithmetic label per (V-cycle precision, outer apply)
 DTYPE = {("fp64", "fp64"): "f64", ("mixed", "fp64"): "f64+f32", ("mixed_tc", "fp64"): "f64+f32(tf32x3)",
-         ("fp64", "df"): "f64+df32", ("mixed", "df"): "f64+df32+f32", ("mixed_tc", "df"): "f64+df32+f32(tf32x3)"}
+         ("mixed_tf32", "fp64"): "f64+f32(tf32)",
+         ("fp64", "df"): "f64+df32", ("mixed", "df"): "f64+df32+f32", ("mixed_tc", "df"): "f64+df32+f32(tf32x3)",
+         ("mixed_tf32", "df"): "f64+df32+f32(tf32)"}
 # the solve's variants compared in the extras: label -> (V-cycle precision, outer apply)
 VARIANTS = {"fp64_plain": ("fp64", "fp64"), "mixed": ("mixed", "fp64"), "mixed_tc": ("mixed_tc", "fp64"),
-            "mixed_df": ("mixed", "df")}
+            "mixed_tf32": ("mixed_tf32", "fp64"), "mixed_df": ("mixed", "df")}
 BATCH_OPTS = dict(smoother="FA", overlap="l", variable_v=True)
 BATCH_NAME = "batched_64grids_4rhs_3d_P4-32_aspect1-16"
 

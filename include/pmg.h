@@ -65,7 +65,10 @@ enum { PMG_WEIGHT_UNWEIGHTED = 0, PMG_WEIGHT_ARITHMETIC = 1, PMG_WEIGHT_CUBIC = 
  * the patch transforms on the SIMT cores (MIXED) or on the tensor cores (MIXED_TC:
  * mma.sync TF32 with the 3xTF32 split, i.e. fp32-level products and fp32
  * accumulation; 3-D patches of at most 32 nodes per axis, others stay SIMT). */
-enum { PMG_PREC_FP64 = 0, PMG_PREC_MIXED = 1, PMG_PREC_MIXED_TC = 2 };
+enum { PMG_PREC_FP64 = 0, PMG_PREC_MIXED = 1, PMG_PREC_MIXED_TC = 2, PMG_PREC_MIXED_TF32 = 3 };
+/* PMG_PREC_MIXED_TF32: as MIXED_TC with one TF32 product per multiply-add (10-bit
+ * operand mantissas, fp32 accumulation): a lower-precision preconditioner whose
+ * effect on the iteration count the flexible CG absorbs. */
 /* Preconditioner of the CG iteration (Algorithm 2). */
 enum { PMG_PC_VCYCLE = 0, PMG_PC_NONE = 1 };
 /* Arithmetic of the CG's operator apply (spec extension): FP64, or

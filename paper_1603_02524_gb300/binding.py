@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libpmg.so")
 SMOOTHER = {"EA": 0, "FA": 1}
 OVERLAP = {"0": 0, "l": 1, "lf": 2}
 WEIGHTING = {"unweighted": 0, "arithmetic": 1, "cubic": 3, "quintic": 5}
-PRECISION = {"fp64": 0, "mixed": 1, "mixed_tc": 2}
+PRECISION = {"fp64": 0, "mixed": 1, "mixed_tc": 2, "mixed_tf32": 3}
 
 STATUS = {0: "PMG_OK", -1: "PMG_EINVAL", -2: "PMG_ENOMEM", -3: "PMG_ECUDA", -4: "PMG_ENOCONV",
           -5: "PMG_EBREAKDOWN", -6: "PMG_ENAN", -7: "PMG_ETIMEOUT"}

@@ -201,7 +201,7 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], 
 
 template <int N>
 __device__ __forceinline__ void line_pass_mma(float* buf, const float* M, int nlines, int lo_stride,
-                                              int lo_count, int hi_stride, int stride) {
+                                              int lo_count, int hi_stride, int stride, bool split3) {
   constexpr int P8 = (N + 7) / 8 * 8, KT = P8 / 8, NT = P8 / 8;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int g = lane >> 2, t = lane & 3;
@@ -215,7 +215,7 @@ __device__ __forceinline__ void line_pass_mma(float* buf, const float* M, int nl
       for (int j = 0; j < 2; ++j) {
         const float b = M[(kt * 8 + t + 4 * j) * P8 + nt * 8 + g];
         bh[kt][nt][j] = to_tf32(b);
-        bl[kt][nt][j] = to_tf32(b - __uint_as_float(bh[kt][nt][j]));
+        bl[kt][nt][j] = split3 ? to_tf32(b - __uint_as_float(bh[kt][nt][j])) : 0u;
       }
   const int mtiles = (nlines + 15) / 16;
   for (int mt = warp; mt < mtiles; mt += nwarps) {
@@ -238,13 +238,18 @@ __device__ __forceinline__ void line_pass_mma(float* buf, const float* M, int nl
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         ah[i] = to_tf32(x[i]);
-        al[i] = to_tf32(x[i] - __uint_as_float(ah[i]));
+        al[i] = split3 ? to_tf32(x[i] - __uint_as_float(ah[i])) : 0u;
       }
+      if (split3) {
 #pragma unroll
-      for (int nt = 0; nt < NT; ++nt) {
-        mma_tf32(acc[nt], al, bh[kt][nt][0], bh[kt][nt][1]);
-        mma_tf32(acc[nt], ah, bl[kt][nt][0], bl[kt][nt][1]);
-        mma_tf32(acc[nt], ah, bh[kt][nt][0], bh[kt][nt][1]);
+        for (int nt = 0; nt < NT; ++nt) {
+          mma_tf32(acc[nt], al, bh[kt][nt][0], bh[kt][nt][1]);
+          mma_tf32(acc[nt], ah, bl[kt][nt][0], bl[kt][nt][1]);
+          mma_tf32(acc[nt], ah, bh[kt][nt][0], bh[kt][nt][1]);
+        }
+      } else {
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) mma_tf32(acc[nt], ah, bh[kt][nt][0], bh[kt][nt][1]);
       }
     }
     __syncwarp();
@@ -291,9 +296,9 @@ constexpr int fdm_threads() {
 // One line pass along an axis: tensor cores (fp32, TC) or SIMT (general / even-odd).
 template <typename T, int N, bool FORWARD, bool TC>
 __device__ __forceinline__ void pass(bool sym, T* buf, const T* M, int nlines, int lo_stride, int lo_count,
-                                     int hi_stride, int stride) {
+                                     int hi_stride, int stride, bool split3 = true) {
   if constexpr (TC) {
-    line_pass_mma<N>(buf, M, nlines, lo_stride, lo_count, hi_stride, stride);
+    line_pass_mma<N>(buf, M, nlines, lo_stride, lo_count, hi_stride, stride, split3);
   } else {
     axis_pass<T, N, FORWARD>(sym, buf, M, nlines, lo_stride, lo_count, hi_stride, stride);
   }
@@ -312,17 +317,17 @@ template <typename T, int NA, int NB, int NC, bool TC>
 __device__ __forceinline__ void patch_compute(T* buf, T* const (&Sq)[3], T* const (&Wq)[3], const T* la,
                                               const T* lb, const T* lc, const bool (&sym)[3],
                                               const long long* off, const long long* rowoff,
-                                              T* __restrict__ u) {
+                                              T* __restrict__ u, bool split3 = true) {
   constexpr int NN = NA * NB * NC;
   // forward transforms, then the scaling by 1 / (lambda_a + lambda_b + lambda_c)
   // (SIMT: folded into the last forward pass)
-  pass<T, NA, true, TC>(sym[0], buf, Sq[0], NB * NC, NA, NB * NC, 0, 1);
+  pass<T, NA, true, TC>(sym[0], buf, Sq[0], NB * NC, NA, NB * NC, 0, 1, split3);
   __syncthreads();
   if constexpr (TC) {
-    pass<T, NB, true, TC>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA);
+    pass<T, NB, true, TC>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA, split3);
     __syncthreads();
     if (NC > 1) {
-      pass<T, NC, true, TC>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB);
+      pass<T, NC, true, TC>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB, split3);
       __syncthreads();
     }
     for (int t = threadIdx.x; t < NN; t += blockDim.x) {
@@ -342,12 +347,12 @@ __device__ __forceinline__ void patch_compute(T* buf, T* const (&Sq)[3], T* cons
   }
   __syncthreads();
   if (NC > 1) {
-    pass<T, NC, false, TC>(sym[2], buf, Wq[2], NA * NB, 1, NA * NB, 0, NA * NB);
+    pass<T, NC, false, TC>(sym[2], buf, Wq[2], NA * NB, 1, NA * NB, 0, NA * NB, split3);
     __syncthreads();
   }
-  pass<T, NB, false, TC>(sym[1], buf, Wq[1], NA * NC, 1, NA, NA * NB, NA);
+  pass<T, NB, false, TC>(sym[1], buf, Wq[1], NA * NC, 1, NA, NA * NB, NA, split3);
   __syncthreads();
-  pass<T, NA, false, TC>(sym[0], buf, Wq[0], NB * NC, NA, NB * NC, 0, 1);
+  pass<T, NA, false, TC>(sym[0], buf, Wq[0], NB * NC, NA, NB * NC, 0, 1, split3);
   __syncthreads();
 
   for (int t = threadIdx.x; t < NN; t += blockDim.x) {
@@ -446,7 +451,7 @@ fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restric
   }
   __syncthreads();
 
-  patch_compute<T, NA, NB, NC, TC>(buf, Sq, Wq, la, lb, lc, sym, off, rowoff, u);
+  patch_compute<T, NA, NB, NC, TC>(buf, Sq, Wq, la, lb, lc, sym, off, rowoff, u, fam.tc != 2);
 }
 
 // ---------------------------------------------------------------------------

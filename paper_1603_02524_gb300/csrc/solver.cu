@@ -192,7 +192,9 @@ void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTab
   dev.r = dev_alloc<T>(own, dm.ndof);
   if (l == 0) return;
   // tensor-core line passes (fp32, 3-D) apply the full tables: unfold even-odd ones
-  const int tc = (sizeof(T) == 4 && h.opt.precision == PMG_PREC_MIXED_TC && dm.dim == 3) ? 1 : 0;
+  const int tc = (sizeof(T) == 4 && dm.dim == 3)
+                     ? (h.opt.precision == PMG_PREC_MIXED_TC ? 1 : (h.opt.precision == PMG_PREC_MIXED_TF32 ? 2 : 0))
+                     : 0;
   std::vector<AxisTables> ecu, fcu;
   const std::vector<AxisTables>& E = tc ? (ecu = ec) : ec;
   const std::vector<AxisTables>& F = tc ? (fcu = fc) : fc;
@@ -811,7 +813,8 @@ int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
   if (o.ns_pre < 0 || o.ns_post < 0 || o.max_iter < 1 || !(o.omega > 0.0)) return PMG_EINVAL;
   for (int l = 0; l < 8; ++l)
     if (!(o.omega_level[l] >= 0.0) || !(o.tau_level[l] >= 0.0) || o.tau_level[l] > 1.0) return PMG_EINVAL;
-  if (o.precision != PMG_PREC_FP64 && o.precision != PMG_PREC_MIXED && o.precision != PMG_PREC_MIXED_TC)
+  if (o.precision != PMG_PREC_FP64 && o.precision != PMG_PREC_MIXED && o.precision != PMG_PREC_MIXED_TC &&
+      o.precision != PMG_PREC_MIXED_TF32)
     return PMG_EINVAL;
   if (o.preconditioner != PMG_PC_VCYCLE && o.preconditioner != PMG_PC_NONE) return PMG_EINVAL;
   if (o.outer_apply != PMG_OUTER_FP64 && o.outer_apply != PMG_OUTER_DF) return PMG_EINVAL;
