@@ -140,20 +140,25 @@ __device__ __forceinline__ float recip(float s) { return rcp_approx(s); }
 // (l % lo_count) * lo_stride + (l / lo_count) * hi_stride, nodes `stride` apart.
 // SCALE (the last forward pass): output i of line l is multiplied by
 // 1 / (lsum(l) + lq[i]), the inverse eigenvalue sum of the fast diagonalisation.
-template <typename T, int N, bool FORWARD, bool SCALE = false, typename LS = int>
+// SCALE = 2: the inverse eigenvalue sums come from a table (lq + lsum(l) + i * istride).
+template <typename T, int N, bool FORWARD, int SCALE = 0, typename LS = int>
 __device__ __forceinline__ void axis_pass(bool sym, T* buf, const T* M, int nlines, int lo_stride,
                                           int lo_count, int hi_stride, int stride,
-                                          const T* lq = nullptr, LS lsum = LS()) {
+                                          const T* lq = nullptr, LS lsum = LS(), int istride = 0) {
   for (int l = threadIdx.x; l < nlines; l += blockDim.x) {
     const int base = (l % lo_count) * lo_stride + (l / lo_count) * hi_stride;
     T v[N], out[N];
 #pragma unroll
     for (int a = 0; a < N; ++a) v[a] = buf[base + a * stride];
     line_transform<T, N, FORWARD>(sym, M, v, out);
-    if constexpr (SCALE) {
+    if constexpr (SCALE == 1) {
       const T s0 = lsum(l);
 #pragma unroll
       for (int i = 0; i < N; ++i) out[i] *= recip(s0 + lq[i]);
+    } else if constexpr (SCALE == 2) {
+      const T* tb = lq + lsum(l);
+#pragma unroll
+      for (int i = 0; i < N; ++i) out[i] *= __ldg(tb + i * istride);
     }
 #pragma unroll
     for (int i = 0; i < N; ++i) buf[base + i * stride] = out[i];
@@ -317,7 +322,8 @@ template <typename T, int NA, int NB, int NC, bool TC>
 __device__ __forceinline__ void patch_compute(T* buf, T* const (&Sq)[3], T* const (&Wq)[3], const T* la,
                                               const T* lb, const T* lc, const bool (&sym)[3],
                                               const long long* off, const long long* rowoff,
-                                              T* __restrict__ u, bool split3 = true) {
+                                              T* __restrict__ u, bool split3 = true,
+                                              const T* invp = nullptr) {
   constexpr int NN = NA * NB * NC;
   // forward transforms, then the scaling by 1 / (lambda_a + lambda_b + lambda_c)
   // (SIMT: folded into the last forward pass)
@@ -338,12 +344,20 @@ __device__ __forceinline__ void patch_compute(T* buf, T* const (&Sq)[3], T* cons
     axis_pass<T, NB, true>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA);
     __syncthreads();
     // line l = (a, b) = (l % NA, l / NA), outputs along c
-    axis_pass<T, NC, true, true>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB, lc,
-                                 [&](int l) { return la[l % NA] + lb[l / NA]; });
+    if (invp)
+      axis_pass<T, NC, true, 2>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB, invp,
+                                [](int l) { return l; }, NA * NB);
+    else
+      axis_pass<T, NC, true, 1>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB, lc,
+                                [&](int l) { return la[l % NA] + lb[l / NA]; });
   } else {
     // 2-D: line l = (a, c) = (l % NA, l / NA), outputs along b
-    axis_pass<T, NB, true, true>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA, lb,
-                                 [&](int l) { return la[l % NA] + lc[l / NA]; });
+    if (invp)
+      axis_pass<T, NB, true, 2>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA, invp,
+                                [](int l) { return l % NA + (l / NA) * NA * NB; }, NA);
+    else
+      axis_pass<T, NB, true, 1>(sym[1], buf, Sq[1], NA * NC, 1, NA, NA * NB, NA, lb,
+                                [&](int l) { return la[l % NA] + lc[l / NA]; });
   }
   __syncthreads();
   if (NC > 1) {
@@ -451,7 +465,13 @@ fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restric
   }
   __syncthreads();
 
-  patch_compute<T, NA, NB, NC, TC>(buf, Sq, Wq, la, lb, lc, sym, off, rowoff, u, fam.tc != 2);
+  const T* invp = nullptr;      // precomputed inverse eigenvalue sums of this patch's combination
+  if (fam.inv) {
+    const int combo = (fam.uid[2][pidx[2]] * fam.ucount[1] + fam.uid[1][pidx[1]]) * fam.ucount[0] +
+                      fam.uid[0][pidx[0]];
+    invp = fam.inv + (size_t)combo * NN;
+  }
+  patch_compute<T, NA, NB, NC, TC>(buf, Sq, Wq, la, lb, lc, sym, off, rowoff, u, fam.tc != 2, invp);
 }
 
 // ---------------------------------------------------------------------------

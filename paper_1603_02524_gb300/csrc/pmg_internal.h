@@ -102,6 +102,12 @@ struct FdmFamily {
   T* scratch = nullptr;
   int scratch_ctas = 0;
   long long scratch_stride = 0;
+  // FP64: 1 / (lambda_a + lambda_b + lambda_c) precomputed per combination of
+  // distinct axis eigenvalue sets (uid[q][p]: set of position p on axis q; few
+  // sets on uniform grids); null where the combinations would be too many
+  const T* inv = nullptr;
+  const int* uid[3] = {nullptr, nullptr, nullptr};
+  int ucount[3] = {1, 1, 1};
 };
 
 struct LevelDims {

@@ -180,6 +180,55 @@ void attach_scratch(Hier& h, FdmFamily<T>& fam, std::vector<void*>& own) {
   fam.scratch = dev_alloc<T>(own, (size_t)fam.scratch_ctas * fam.scratch_stride);
 }
 
+// FP64 families: precompute 1 / ((lambda_a + lambda_b) + lambda_c) (the kernel's sum
+// order, IEEE division) for every combination of distinct per-axis eigenvalue sets;
+// on uniform grids an axis has at most three (the two walls, the interior), so the
+// table is small and the patch kernel replaces a Newton reciprocal per node by one
+// load.  Skipped when the combinations would take more than 32 MB.
+template <typename T>
+void attach_inverse_table(FdmFamily<T>& fam, const AxisTables* const (&tab)[3], std::vector<void*>& own) {
+  if (sizeof(T) != 8 || fam.tc) return;
+  std::vector<int> uid[3];
+  std::vector<std::vector<double>> rep[3];
+  long long combos = 1;
+  for (int q = 0; q < 3; ++q) {
+    const int n = fam.ax[q].n, count = fam.ax[q].count;
+    std::map<std::vector<double>, int> ids;
+    uid[q].resize(count);
+    for (int p = 0; p < count; ++p) {
+      std::vector<double> lam = tab[q] ? std::vector<double>(tab[q]->lam.begin() + (size_t)p * n,
+                                                             tab[q]->lam.begin() + (size_t)(p + 1) * n)
+                                       : std::vector<double>(1, 0.0);
+      auto it = ids.find(lam);
+      if (it == ids.end()) {
+        it = ids.emplace(lam, (int)rep[q].size()).first;
+        rep[q].push_back(lam);
+      }
+      uid[q][p] = it->second;
+    }
+    combos *= (long long)rep[q].size();
+  }
+  const int na = fam.ax[0].n, nb = fam.ax[1].n, nc = fam.ax[2].n;
+  const long long nn = (long long)na * nb * nc;
+  if (combos * nn * (long long)sizeof(T) > (32LL << 20)) return;
+  std::vector<double> inv((size_t)(combos * nn));
+  for (int i2 = 0; i2 < (int)rep[2].size(); ++i2)
+    for (int i1 = 0; i1 < (int)rep[1].size(); ++i1)
+      for (int i0 = 0; i0 < (int)rep[0].size(); ++i0) {
+        const long long combo = ((long long)i2 * (long long)rep[1].size() + i1) * (long long)rep[0].size() + i0;
+        double* dst = &inv[(size_t)(combo * nn)];
+        for (int c = 0; c < nc; ++c)
+          for (int b = 0; b < nb; ++b)
+            for (int a = 0; a < na; ++a)
+              dst[((size_t)c * nb + b) * na + a] = 1.0 / ((rep[0][i0][a] + rep[1][i1][b]) + rep[2][i2][c]);
+      }
+  fam.inv = dev_upload<T>(own, inv);
+  for (int q = 0; q < 3; ++q) {
+    fam.uid[q] = dev_upload_int(own, uid[q]);
+    fam.ucount[q] = (int)rep[q].size();
+  }
+}
+
 template <typename T>
 void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTables>& ec,
                      const std::vector<AxisTables>& fc) {
@@ -215,6 +264,9 @@ void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTab
       }
     }
     attach_scratch<T>(h, fam, own);
+    const AxisTables* tab[3] = {nullptr, nullptr, nullptr};
+    for (int q = 0; q < dm.dim; ++q) tab[q] = &E[q];
+    attach_inverse_table<T>(fam, tab, own);
     dev.ea = fam;
   } else {
     for (int nrm = 0; nrm < dm.dim; ++nrm) {
@@ -231,6 +283,10 @@ void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTab
       }
       for (; q < 3; ++q) fam.ax[q] = trivial_axis<T>(own);
       attach_scratch<T>(h, fam, own);
+      const AxisTables* tab[3] = {&F[nrm], nullptr, nullptr};
+      for (int d = 0, qq = 1; d < dm.dim; ++d)
+        if (d != nrm) tab[qq++] = &E[d];
+      attach_inverse_table<T>(fam, tab, own);
       dev.fa[nrm] = fam;
     }
   }
