@@ -519,7 +519,7 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
     # scaled by patches; only for the kernel version that was captured
     traffic = None
     if fam == -1 and fp64_main and w.P == 8 and w.dim == 3:
-        traffic = (383.11e6 + 152.65e6) / 32768 * nelem
+        traffic = (383.47e6 + 162.46e6) / 32768 * nelem
     line["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                         "frac": ach / peak, "traffic": traffic,
                         "kernel": (f"fdm_kernel<{tname},{nn},{nn},{nn}> (EA patch solve, P={w.P})"
