@@ -66,9 +66,11 @@ enum { PMG_WEIGHT_UNWEIGHTED = 0, PMG_WEIGHT_ARITHMETIC = 1, PMG_WEIGHT_CUBIC = 
  * mma.sync TF32 with the 3xTF32 split, i.e. fp32-level products and fp32
  * accumulation; 3-D patches of at most 32 nodes per axis, others stay SIMT). */
 enum { PMG_PREC_FP64 = 0, PMG_PREC_MIXED = 1, PMG_PREC_MIXED_TC = 2, PMG_PREC_MIXED_TF32 = 3 };
-/* PMG_PREC_MIXED_TF32: as MIXED_TC with one TF32 product per multiply-add (10-bit
- * operand mantissas, fp32 accumulation): a lower-precision preconditioner whose
- * effect on the iteration count the flexible CG absorbs. */
+/* PMG_PREC_MIXED_TF32: one TF32 product per multiply-add (10-bit operand
+ * mantissas, fp32 accumulation), the patch line passes as tcgen05 MMAs with the
+ * operands in shared memory and the accumulators in tensor memory (3-D patches
+ * of at most 32 nodes per axis; others stay SIMT): a lower-precision
+ * preconditioner whose effect on the iteration count the flexible CG absorbs. */
 /* Preconditioner of the CG iteration (Algorithm 2). */
 enum { PMG_PC_VCYCLE = 0, PMG_PC_NONE = 1 };
 /* Arithmetic of the CG's operator apply (spec extension): FP64, or
@@ -329,6 +331,14 @@ int pmg_schwarz_sweep_fma(pmg_hier h, int level, int family, double* fma);
 /* Number of CUDA kernels this library has launched in this process so far
  * (all hierarchies, all devices); for counting launches in a timed region. */
 unsigned long long pmg_kernel_launches(void);
+
+/* Number of thread blocks of the tcgen05 patch kernel (PMG_PREC_MIXED_TF32)
+ * that gave up waiting for their tensor-core MMAs (each wait is bounded at about
+ * one second; such a block stops early and its corrections are incomplete) since
+ * the last call, on the current device; the count is reset.  Synchronises the
+ * device.  Returns PMG_OK, or PMG_EINVAL for a null pointer, PMG_ECUDA on a CUDA
+ * error. */
+int pmg_tc_timeouts(unsigned int* count);
 
 #ifdef __cplusplus
 }

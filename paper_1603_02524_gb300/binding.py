@@ -28,7 +28,8 @@ EXPORTS = ["pmg_options_default", "pmg_grid_create", "pmg_grid_destroy", "pmg_gr
            "pmg_last_error", "pmg_schwarz_sweep", "pmg_kernel_launches", "pmg_coarse_solve_static",
            "pmg_schwarz_sweep_fma", "pmg_schwarz_sweep_native", "pmg_mlp_forward",
            "pmg_mlp_backward", "pmg_mlp_adam", "pmg_batch_create", "pmg_batch_solve",
-           "pmg_batch_destroy", "pmg_batch_last_error", "pmg_hierarchy_autotune", "pmg_tuned_threads"]
+           "pmg_batch_destroy", "pmg_batch_last_error", "pmg_hierarchy_autotune", "pmg_tuned_threads",
+           "pmg_tc_timeouts"]
 
 
 class PmgOptions(ctypes.Structure):
@@ -89,6 +90,7 @@ def load(path: str | None = None):
         "pmg_last_error": (ctypes.c_char_p, [vp]),
         "pmg_schwarz_sweep": (i, [vp, i, i, vp, vp, vp]),
         "pmg_kernel_launches": (ctypes.c_ulonglong, []),
+        "pmg_tc_timeouts": (i, [ctypes.POINTER(ctypes.c_uint)]),
         "pmg_coarse_solve_static": (i, [vp, vp, vp, vp]),
         "pmg_schwarz_sweep_fma": (i, [vp, i, i, ctypes.POINTER(ctypes.c_double)]),
         "pmg_schwarz_sweep_native": (i, [vp, i, i, vp]),
@@ -134,6 +136,14 @@ def options(smoother="EA", overlap="l", weighting="quintic", ns=(1, 1), variable
     o.preconditioner = {"vcycle": 0, "none": 1}[preconditioner]
     o.outer_apply = {"fp64": 0, "df": 1}[outer_apply]
     return o
+
+
+def tc_timeouts() -> int:
+    """Blocks of the tcgen05 patch kernel that gave up waiting for their MMAs
+    since the last call (reset by the call; synchronises the device)."""
+    n = ctypes.c_uint(0)
+    _check("pmg_tc_timeouts", load().pmg_tc_timeouts(ctypes.byref(n)))
+    return int(n.value)
 
 
 def _check(fn, st, hier=None):

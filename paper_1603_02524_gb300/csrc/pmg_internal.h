@@ -89,6 +89,10 @@ struct FdmAxis {
 // Largest CTA any patch-kernel launch may use (the autotuner's candidates stay
 // within it; it caps registers at 128 per thread).
 constexpr int kFdmMaxThreads = 512;
+// Smallest patch (nodes) that the tcgen05 patch kernel takes (PMG_PREC_MIXED_TF32);
+// measured on GB300: 13^3 EA patches break even with the SIMT kernel, smaller
+// ones run about 2x faster on the SIMT kernel.
+constexpr long long kTcMinPatchNodes = 13 * 13 * 13;
 
 template <typename T>
 struct FdmFamily {

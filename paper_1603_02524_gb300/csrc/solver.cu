@@ -24,6 +24,7 @@ std::atomic<unsigned long long> g_launches{0};
 int fdm_dispatch_d3(const LevelDims&, const FdmFamily<double>&, const double*, double*, cudaStream_t);
 int fdm_dispatch_d2(const LevelDims&, const FdmFamily<double>&, const double*, double*, cudaStream_t);
 int fdm_dispatch_f3(const LevelDims&, const FdmFamily<float>&, const float*, float*, cudaStream_t);
+int tc_timeouts_take(unsigned int* out);
 int fdm_dispatch_f2(const LevelDims&, const FdmFamily<float>&, const float*, float*, cudaStream_t);
 
 template <>
@@ -106,10 +107,25 @@ FdmAxis<T> trivial_axis(std::vector<void*>& owned) {
   return ax;
 }
 
-// scale: omega for the first patch-buffer axis (folds the damping into W), 1 otherwise
+// x rounded to the nearest tf32 value (8 exponent bits, 10 stored mantissa bits;
+// ties to even), as an fp32 value in a double
+double round_to_tf32(double x) {
+  float f = (float)x;
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0xFFFu + ((u >> 13) & 1u);
+    u &= 0xFFFFE000u;
+  }
+  std::memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+// scale: omega for the first patch-buffer axis (folds the damping into W), 1 otherwise;
+// tf32: tables rounded to tf32 for the tensor-core patch kernel
 template <typename T>
 FdmAxis<T> upload_axis(std::vector<void*>& owned, const AxisTables& t, const Axis1DHost& a, int phys,
-                       double scale) {
+                       double scale, bool tf32 = false) {
   FdmAxis<T> ax{};
   ax.n = t.n;
   ax.count = t.count;
@@ -117,9 +133,13 @@ FdmAxis<T> upload_axis(std::vector<void*>& owned, const AxisTables& t, const Axi
   ax.N = a.Ne * a.NP;
   ax.periodic = a.periodic ? 1 : 0;
   ax.phys = phys;
-  ax.S = dev_upload<T>(owned, t.S);
-  std::vector<double> W(t.W);
+  std::vector<double> S(t.S), W(t.W);
   for (double& x : W) x *= scale;
+  if (tf32) {
+    for (double& x : S) x = round_to_tf32(x);
+    for (double& x : W) x = round_to_tf32(x);
+  }
+  ax.S = dev_upload<T>(owned, S);
   ax.W = dev_upload<T>(owned, W);
   ax.lam = dev_upload<T>(owned, t.lam);
   ax.sym = dev_upload_int(owned, t.sym);
@@ -241,9 +261,15 @@ void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTab
   dev.r = dev_alloc<T>(own, dm.ndof);
   if (l == 0) return;
   // tensor-core line passes (fp32, 3-D) apply the full tables: unfold even-odd ones
-  const int tc = (sizeof(T) == 4 && dm.dim == 3)
-                     ? (h.opt.precision == PMG_PREC_MIXED_TC ? 1 : (h.opt.precision == PMG_PREC_MIXED_TF32 ? 2 : 0))
-                     : 0;
+  int tc = (sizeof(T) == 4 && dm.dim == 3)
+               ? (h.opt.precision == PMG_PREC_MIXED_TC ? 1 : (h.opt.precision == PMG_PREC_MIXED_TF32 ? 2 : 0))
+               : 0;
+  if (tc == 2) {
+    // the tcgen05 kernel pays a fixed latency per line pass; small patches stay on
+    // the SIMT kernel (folded tables), which is faster there
+    const long long nn = (long long)(h.opt.smoother == PMG_SMOOTHER_EA ? ec[0].n : fc[0].n) * ec[1].n * ec[2].n;
+    if (nn < kTcMinPatchNodes) tc = 0;
+  }
   std::vector<AxisTables> ecu, fcu;
   const std::vector<AxisTables>& E = tc ? (ecu = ec) : ec;
   const std::vector<AxisTables>& F = tc ? (fcu = fc) : fc;
@@ -257,7 +283,7 @@ void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTab
     fam.tc = tc;
     for (int q = 0; q < 3; ++q) {
       if (q < dm.dim) {
-        fam.ax[q] = upload_axis<T>(own, E[q], ax[q], q, q == 0 ? level_omega(h.opt, l) : 1.0);
+        fam.ax[q] = upload_axis<T>(own, E[q], ax[q], q, q == 0 ? level_omega(h.opt, l) : 1.0, tc == 2);
         fam.count_total *= E[q].count;
       } else {
         fam.ax[q] = trivial_axis<T>(own);
@@ -272,12 +298,12 @@ void build_level_dev(Hier& h, int l, LevelDev<T>& dev, const std::vector<AxisTab
     for (int nrm = 0; nrm < dm.dim; ++nrm) {
       FdmFamily<T> fam{};
       fam.tc = tc;
-      fam.ax[0] = upload_axis<T>(own, F[nrm], ax[nrm], nrm, level_omega(h.opt, l));
+      fam.ax[0] = upload_axis<T>(own, F[nrm], ax[nrm], nrm, level_omega(h.opt, l), tc == 2);
       fam.count_total = F[nrm].count;
       int q = 1;
       for (int d = 0; d < dm.dim; ++d) {
         if (d == nrm) continue;
-        fam.ax[q] = upload_axis<T>(own, E[d], ax[d], d, 1.0);
+        fam.ax[q] = upload_axis<T>(own, E[d], ax[d], d, 1.0, tc == 2);
         fam.count_total *= E[d].count;
         ++q;
       }
@@ -609,7 +635,11 @@ int tune_family(Hier& h, int l, FdmFamily<T>& fam, LevelDev<T>& d, cudaStream_t 
   const LevelDims& dm = h.dims[l];
   PMG_CUDA(cudaMemsetAsync(d.f, 0, sizeof(T) * dm.ndof, s));
   PMG_CUDA(cudaMemsetAsync(d.u, 0, sizeof(T) * dm.ndof, s));
-  static const int cand[] = {64, 96, 128, 160, 192, 256, 320, 384, 448, 512};
+  static const int cand_simt[] = {64, 96, 128, 160, 192, 256, 320, 384, 448, 512};
+  static const int cand_tc[] = {128, 256, 384, 512};  // tcgen05 kernel: whole warp quarters
+  const bool tc5 = sizeof(T) == 4 && fam.tc == 2 && dm.dim == 3;
+  const int* cand = tc5 ? cand_tc : cand_simt;
+  const int ncand = tc5 ? 4 : 10;
   cudaEvent_t e0, e1;
   PMG_CUDA(cudaEventCreate(&e0));
   PMG_CUDA(cudaEventCreate(&e1));
@@ -619,7 +649,8 @@ int tune_family(Hier& h, int l, FdmFamily<T>& fam, LevelDev<T>& d, cudaStream_t 
   const int nvar = sizeof(T) == 4 && !fam.tc ? 2 : 1;
   try {
     for (int v = 0; v < nvar; ++v) {
-      for (int c : cand) {
+      for (int ci = 0; ci < ncand; ++ci) {
+        const int c = cand[ci];
         if (c > kFdmMaxThreads) continue;
         fam.threads = c;
         fam.variant = nvar == 2 ? v : -1;
@@ -1253,6 +1284,11 @@ const char* pmg_status_string(int status) {
 const char* pmg_last_error(pmg_hier hh) { return hh ? H(hh)->err.c_str() : ""; }
 
 unsigned long long pmg_kernel_launches(void) { return g_launches.load(); }
+
+int pmg_tc_timeouts(unsigned int* count) {
+  if (!count) return PMG_EINVAL;
+  return tc_timeouts_take(count);
+}
 
 int pmg_schwarz_sweep_native(pmg_hier hh, int level, int family, void* stream) {
   Hier* h = H(hh);
