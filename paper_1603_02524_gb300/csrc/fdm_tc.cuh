@@ -32,8 +32,9 @@
 //
 // Precision: tf32 products (10-bit operand mantissas) with fp32 accumulation;
 // the tables are rounded to tf32 on the host, the operands between passes when
-// they are stored, and the gathered residual is truncated by the tensor core.  The preconditioner is applied
-// inside a flexible CG whose residual, operator and inner products stay FP64.
+// they are stored, and the gathered residual is truncated by the tensor core.
+// The preconditioner is applied inside a flexible CG whose residual, operator
+// and inner products stay FP64.
 #pragma once
 
 #include "fdm_kernel.cuh"
@@ -92,7 +93,12 @@ struct TcRows {
   static constexpr int W = 32 / R;
 };
 
-__device__ __forceinline__ float round_tf32(float x) { return __uint_as_float(to_tf32(x)); }
+// x rounded to tf32 (nearest, ties away from zero) by integer operations on its
+// bits: add half a unit of the 13 dropped mantissa bits to the magnitude, then
+// clear them (finite x).
+__device__ __forceinline__ float round_tf32(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
 
 // A operand element (row, K index k), 8-row groups `sbo` bytes apart.
 __device__ __forceinline__ int a_index(int row, int k, uint32_t sbo) {
@@ -133,13 +139,16 @@ __device__ __forceinline__ bool tc_pass(float* A, const float* B, uint64_t* mbar
   __syncthreads();
   if (threadIdx.x == 0) {
     umma::fence_after_sync();
-    const uint32_t a0 = umma::smem_u32(A), b0 = umma::smem_u32(B);
-#pragma unroll 1
+    // descriptors of the first tile and K step; later ones advance the start
+    // address field (bytes / 16; operands lie below 256 KB, so no carry)
+    const uint64_t ad = umma::smem_desc(umma::smem_u32(A), G::LBO, SB);
+    const uint64_t bd = umma::smem_desc(umma::smem_u32(B), 128, G::tsbo(n));
+#pragma unroll
     for (int t = 0; t < MT; ++t)
 #pragma unroll
       for (int ks = 0; ks < KS; ++ks)
-        umma::mma_tf32(tmem + (uint32_t)(t * NPD), umma::smem_desc(a0 + t * 16 * SB + ks * 2 * G::LBO, G::LBO, SB),
-                       umma::smem_desc(b0 + ks * 256, 128, G::tsbo(n)), idesc, ks > 0);
+        umma::mma_tf32(tmem + (uint32_t)(t * NPD), ad + (uint64_t)((t * 16 * SB + ks * 2 * G::LBO) >> 4),
+                       bd + (uint64_t)((ks * 256) >> 4), idesc, ks > 0);
     umma::mma_commit(mbar);
   }
   const bool ok = umma::mbar_wait(mbar, phase, 1000000000ull);
@@ -312,10 +321,22 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
       const long long oa = lane < NA ? off[lane] : 0;
       const int lk = (lane >> 2) * 36 + (lane & 3);
       constexpr int S = (int)G::sbo(NA) / 4;
-      for (int row = (tid >> 5) * TcRows<NA>::R + hw; row < NB * NC; row += rstep) {
-        const int b = row % NB, c = row / NB, m = b + G::NBP * c;
-        const long long o = oa + rowoff[row];
-        if (lane < NA) cp_async<4>(A + (m >> 3) * S + (m & 7) * 4 + lk, o >= 0 ? r + o : r, o >= 0);
+      // four rows per step: their row offsets are read before the first copy is issued
+      for (int row0 = (tid >> 5) * TcRows<NA>::R + hw; row0 < NB * NC; row0 += 4 * rstep) {
+        long long ro[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int row = row0 + i * rstep;
+          ro[i] = row < NB * NC ? rowoff[row] : kInvalidOffset;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int row = row0 + i * rstep;
+          const int b = row % NB, c = row / NB, m = b + G::NBP * c;
+          const long long o = oa + ro[i];
+          if (row < NB * NC && lane < NA)
+            cp_async<4>(A + (m >> 3) * S + (m & 7) * 4 + lk, o >= 0 ? r + o : r, o >= 0);
+        }
       }
     }
     cp_async_commit();
@@ -335,9 +356,21 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
       const int hw = (threadIdx.x & 31) / TcRows<NA>::W, lane = (threadIdx.x & 31) % TcRows<NA>::W;
       const int rstep = (blockDim.x >> 5) * TcRows<NA>::R;
       const long long oa = lane < NA ? off[lane] : 0;
-      for (int row = (tid >> 5) * TcRows<NA>::R + hw; row < NB * NC; row += rstep) {
-        const long long o = oa + rowoff[row];
-        if (lane < NA && o >= 0) atomicAdd(u + o, A[row * G::FS + lane]);
+      for (int row0 = (tid >> 5) * TcRows<NA>::R + hw; row0 < NB * NC; row0 += 4 * rstep) {
+        long long ro[4];
+        float v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int row = row0 + i * rstep;
+          const bool in = row < NB * NC && lane < NA;
+          ro[i] = in ? rowoff[row] : kInvalidOffset;
+          v[i] = in ? A[row * G::FS + lane] : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const long long o = oa + ro[i];
+          if (o >= 0) atomicAdd(u + o, v[i]);
+        }
       }
     }
     __syncthreads();                             // staging, offsets and tables are rewritten next
