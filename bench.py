@@ -41,6 +41,19 @@ FP64_PEAK_GFLOPS = 1200.0
 FP32_PEAK_GFLOPS = 74800.0
 
 
+def _tf32_peak_gflops():
+    """Dense tf32 tensor peak: the measured bf16 burst peak (MEASURED_PEAKS.json, else the
+    1.9 PFLOP/s fallback) x the nominal tf32 : bf16 ratio 1/2."""
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["bf16_tflops"]) * 1e3 / 2
+    except (OSError, KeyError, ValueError):
+        return 1900e3 / 2
+
+
+TF32_PEAK_GFLOPS = _tf32_peak_gflops()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -71,7 +84,8 @@ DTYPE = {("fp64", "fp64"): "f64", ("mixed", "fp64"): "f64+f32", ("mixed_tc", "fp
          ("mixed_tf32", "df"): "f64+df32+f32(tf32)"}
 # the solve's variants compared in the extras: label -> (V-cycle precision, outer apply)
 VARIANTS = {"fp64_plain": ("fp64", "fp64"), "mixed": ("mixed", "fp64"), "mixed_tc": ("mixed_tc", "fp64"),
-            "mixed_tf32": ("mixed_tf32", "fp64"), "mixed_df": ("mixed", "df")}
+            "mixed_tf32": ("mixed_tf32", "fp64"), "mixed_df": ("mixed", "df"),
+            "mixed_tf32_df": ("mixed_tf32", "df")}
 BATCH_OPTS = dict(smoother="FA", overlap="l", variable_v=True)
 BATCH_NAME = "batched_64grids_4rhs_3d_P4-32_aspect1-16"
 
@@ -571,11 +585,14 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
         t_o = statistics.mean(tm)
         fl_o = 2.0 * hm.schwarz_sweep_fma(hm.L, fam)
         pk_o = (FP64_PEAK_GFLOPS if prec == "fp64" else FP32_PEAK_GFLOPS) / 1e3
+        if prec == "mixed_tf32" and w.dim == 3 and w.P >= 8:   # tcgen05 patch kernel: tf32 tensor peak
+            pk_o = TF32_PEAK_GFLOPS / 1e3
         entry = {"value": n / (t_o * 1e-3), "unit": "DOF/s", "ms_per_step": t_o, "iterations": itm,
                  "status": rc, "max_rel_diff_between_solutions": rel, "patch_sweep_ms": ms_o,
                  "smoother_gdof_s": n / (ms_o * 1e-3) / 1e9,
                  "smoother_roofline_frac": fl_o / (ms_o * 1e-3) / 1e12 / pk_o,
-                 "smoother_peak": f"{'FP64' if prec == 'fp64' else 'FP32'} FMA, measured"}
+                 "smoother_peak": ("TF32 tensor (measured bf16 x 1/2)" if pk_o * 1e3 == TF32_PEAK_GFLOPS
+                                   else f"{'FP64' if prec == 'fp64' else 'FP32'} FMA, measured")}
         if other == "fp64_plain":
             line["fp64_plain"] = entry
             line["speedup_vs_fp64"] = t_o / line["ms_per_step"]
