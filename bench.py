@@ -66,14 +66,17 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed_tc", "mixed_tf32"],
                     help="arithmetic of the timed solve's V-cycle (the outer CG is always FP64); "
-                         "default fp64, mixed for the batched workload c5")
+                         "default fp64, mixed_tf32 for the batched workload c5")
     ap.add_argument("--autotune", action="store_true",
                     help="autotune the patch kernel's CTA size before timing (always on for c5)")
-    ap.add_argument("--outer-apply", default="fp64", choices=["fp64", "df"],
-                    help="arithmetic of the CG's own operator apply: FP64, or double-float on the FP32 pipes")
+    ap.add_argument("--outer-apply", default=None, choices=["fp64", "df"],
+                    help="arithmetic of the CG's own operator apply: FP64, or double-float on the FP32 "
+                         "pipes; default fp64, df for the batched workload c5")
     args = ap.parse_args()
     if args.precision is None:
-        args.precision = "mixed" if args.workload == "c5" else "fp64"
+        args.precision = "mixed_tf32" if args.workload == "c5" else "fp64"
+    if args.outer_apply is None:
+        args.outer_apply = "df" if args.workload == "c5" else "fp64"
     return args
 
 
@@ -267,7 +270,7 @@ def main_batch(args):
         grid = Grid(w.dim, w.P, w.n_elem, w.spacing, periodic=w.periodic, mu_star=w.mu_star, beta=w.beta)
         grids.append(grid)
         for k in range(w.extra["n_rhs"]):
-            h = Hierarchy(grid, precision=args.precision, **BATCH_OPTS)
+            h = Hierarchy(grid, precision=args.precision, outer_apply=args.outer_apply, **BATCH_OPTS)
             f = syn.gauss_noise(w, seed=w.seed * 8 + k)
             ft = torch.from_numpy(np.ascontiguousarray(f).reshape(-1)).to(dev)
             g = torch.empty_like(ft)
@@ -319,10 +322,11 @@ def main_batch(args):
     line = {"metric": METRIC, "value": world * total / (t_step * 1e-3), "unit": "DOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+            "dtype": DTYPE[(args.precision, args.outer_apply)], "data": "synthetic",
             "config": {"workload": BATCH_NAME, "solves": len(hiers),
                        "grids": len(members), "total_dof": total, "max_dof": max(ndof), "min_dof": min(ndof),
-                       "smoother": "FA_l variable V", "precision": args.precision, "rtol": 1e-10,
+                       "smoother": "FA_l variable V", "precision": args.precision,
+                       "outer_apply": args.outer_apply, "rtol": 1e-10,
                        "iterations_min_median_max": [min(its), int(statistics.median(its)), max(its)],
                        "l2": "flushed between steps (256 MB write); 4 GB of vectors", "one_graph_launch": True,
                        "setup_s": t_setup, "autotune_s": t_tune, "capture_s": t_capture,

@@ -28,10 +28,14 @@ def same_run(u_a, u_b, hist_a, hist_b, precision="fp64"):
     FP64 V-cycle: residual histories to 1e-9, solutions to 1e-11.  fp32 V-cycle: the
     atomic order changes the preconditioned residual at fp32 rounding (~1e-7), the
     history by up to ~1e-5 relative, and the converged solutions by far less than
-    the 1e-10 stopping tolerance (1e-8 of the solution's max-norm)."""
+    the 1e-10 stopping tolerance (1e-8 of the solution's max-norm).  tf32 transforms
+    (mixed_tf32): the operands are rounded to tf32 between line passes, so an fp32-level
+    difference can move a value across a tf32 rounding boundary (2^-11 relative); the
+    history may then differ by up to ~1e-2 relative, the solutions as for fp32."""
     assert len(hist_a) == len(hist_b)
     fp64 = precision == "fp64"
-    assert np.allclose(hist_a, hist_b, rtol=1e-9 if fp64 else 1e-4, atol=1e-13 * hist_a[0])
+    rtol = 1e-9 if fp64 else (2e-2 if precision == "mixed_tf32" else 1e-4)
+    assert np.allclose(hist_a, hist_b, rtol=rtol, atol=1e-13 * hist_a[0])
     scale = float(u_a.abs().max()) or 1.0
     assert float((u_a - u_b).abs().max()) <= (1e-11 if fp64 else 1e-8) * scale
 
@@ -44,6 +48,9 @@ CASES = [
     (2, 8, (4, 3), [[0.25] * 4, [0.3, 0.3, 0.4]], True, 0.0, dict(smoother="EA", precision="mixed")),
     (3, 8, (4, 3, 3), [[0.25] * 4, [1 / 3] * 3, [1 / 3] * 3], False, 0.0,
      dict(smoother="EA", precision="mixed_tc")),
+    # tcgen05 patch kernel (P = 16: 23^3 and 32 x 23 x 23 patches) with the double-float CG apply
+    (3, 16, (2, 2, 2), [[0.5, 0.5], [0.4, 0.6], [0.5, 0.5]], True, 0.5,
+     dict(smoother="FA", precision="mixed_tf32", outer_apply="df")),
 ]
 IDS = [f"{c[0]}d-P{c[1]}-{'per' if c[4] else 'dir'}-{c[6].get('smoother')}-{c[6].get('precision', 'fp64')}"
        for c in CASES]
