@@ -531,6 +531,12 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
     flops = 2.0 * h.schwarz_sweep_fma(h.L, fam)
     paper_flops = 12.0 * nn ** 4 * nelem if fam == -1 else None   # the paper's n^4-per-pass count (EA)
     peak = (FP64_PEAK_GFLOPS if fp64_main else FP32_PEAK_GFLOPS) / 1e3
+    # precision mixed_tf32 on 3-D patches of 13^3 nodes and more: the tcgen05 kernel, whose
+    # contractions run on the tensor cores (tf32 peak)
+    n_a = nn if fam == -1 else 2 * w.P
+    tc5 = args.precision == "mixed_tf32" and w.dim == 3 and n_a * nn * nn >= 13 ** 3
+    if tc5:
+        peak = TF32_PEAK_GFLOPS / 1e3
     ach = flops / (ms * 1e-3) / 1e12
     # DRAM bytes per patch of this kernel from one ncu capture of the same kernel on the
     # 32^3-element P = 8 problem (the ncu summary of fdm_kernel<double,13> under profiles/),
@@ -538,15 +544,19 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
     traffic = None
     if fam == -1 and fp64_main and w.P == 8 and w.dim == 3:
         traffic = (383.47e6 + 162.46e6) / 32768 * nelem
-    line["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+    kname = "fdm_kernel_tc" if tc5 else f"fdm_kernel<{tname},"
+    line["roofline"] = {"bound": "tensor" if tc5 else "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                         "frac": ach / peak, "traffic": traffic,
-                        "kernel": (f"fdm_kernel<{tname},{nn},{nn},{nn}> (EA patch solve, P={w.P})"
-                                   if fam == -1 else
-                                   f"fdm_kernel<{tname},{2 * w.P},{nn},{nn}> (FA patch solve, x faces, P={w.P})"),
+                        "kernel": ((f"{kname}<{nn},{nn},{nn}>" if tc5 else f"{kname}{nn},{nn},{nn}>")
+                                   + f" (EA patch solve, P={w.P})" if fam == -1 else
+                                   (f"{kname}<{2 * w.P},{nn},{nn}>" if tc5 else f"{kname}{2 * w.P},{nn},{nn}>")
+                                   + f" (FA patch solve, x faces, P={w.P})"),
                         "flops_per_launch": flops, "paper_count_flops_per_launch": paper_flops,
-                        "peak_source": ("FP64" if fp64_main else "FP32") + " FMA throughput measured on this "
-                                       "pool's GB300 (FMA-chain probe; nominal FP64 1.25 TFLOP/s); the patch "
-                                       "solve does ~270 flop per 24 B/DOF, far above both ridges"}
+                        "peak_source": ("dense tf32 tensor peak = measured bf16 burst peak x 1/2; flops are "
+                                        "the line passes' multiply-adds x 2 (tables unfolded)" if tc5 else
+                                        ("FP64" if fp64_main else "FP32") + " FMA throughput measured on this "
+                                        "pool's GB300 (FMA-chain probe; nominal FP64 1.25 TFLOP/s); the patch "
+                                        "solve does ~270 flop per 24 B/DOF, far above both ridges")}
     line["smoother"] = {"gdof_s": n / (ms * 1e-3) / 1e9, "ms_patch_sweep": ms,
                         "note": ("EA" if fam == -1 else "FA (one direction)")
                                 + f" patch sweep alone (gather, 6 transforms, weighted scatter), {tname}"}
