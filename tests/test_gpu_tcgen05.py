@@ -141,3 +141,30 @@ def test_tf32_autotune_keeps_results():
     h.schwarz_sweep(h.L, -1, r, u1)
     assert float((u1 - u0).abs().max()) <= 1e-6 * float(u0.abs().max())
     assert no_timeouts()
+
+
+@pytest.mark.parametrize("kind", ["EA", "FA"])
+@pytest.mark.parametrize("P,ne,per", [(8, 12, False), (16, 8, True)], ids=["P8-12cube-dir", "P16-8cube-per"])
+def test_tf32_chunked_patches_match_simt(P, ne, per, kind):
+    """Grids with more patches than resident CTAs: each CTA walks a chunk of consecutive
+    patches and keeps the tables, eigenvalues and offsets of unchanged axis positions.
+    Element widths vary along every axis, so positions differ in their tables.  One
+    smoothing step against the SIMT fp32 kernel (itself checked against the oracle)."""
+    rng = syn.rng(5 + P)
+    sp = []
+    for _ in range(3):
+        w = rng.uniform(0.5, 2.0, size=ne)
+        sp.append(list(w / w.sum()))
+    case = (3, P, (ne,) * 3, sp, per, 0.0)
+    h = make(case, smoother=kind, precision="mixed_tf32")
+    hs = make(case, smoother=kind, precision="mixed")
+    shape = elem_shape(3, (ne,) * 3, P)
+    u, f = rnd(shape, 80), rnd(shape, 81)
+    if per:
+        f -= f.mean()
+    ut, us = to_dev(u), to_dev(u)
+    h.smooth(h.L, ut, to_dev(f), 1)
+    hs.smooth(hs.L, us, to_dev(f), 1)
+    du, ds = from_dev(ut, shape) - u, from_dev(us, shape) - u
+    assert rel_err(du, ds) < TF32_STEP_TOL
+    assert no_timeouts()
