@@ -88,7 +88,10 @@ __device__ __forceinline__ uint64_t globaltimer() {
   return t;
 }
 // Wait for the completion of phase `parity`; gives up after about timeout_ns
-// (returns false) so that a lost completion cannot hang the GPU.
+// (returns false) so that a lost completion cannot hang the GPU.  Each attempt
+// may suspend the thread until the phase completes or for at most the hint
+// (ns), so waiting threads take few issue slots.
+constexpr uint32_t kSuspendHintNs = 20000;
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint64_t timeout_ns) {
   const uint32_t a = smem_u32(mbar);
   uint64_t t0 = 0;
@@ -96,10 +99,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint6
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(kSuspendHintNs)
         : "memory");
     if (done) return true;
     if (it == 0) t0 = globaltimer();
