@@ -225,7 +225,6 @@ __global__ void __launch_bounds__(512)
 fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, float* __restrict__ u,
               unsigned int* timeouts) {
   using G = TcGeom<NA, NB, NC>;
-  constexpr int NN = G::NN;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   float* A = reinterpret_cast<float*>(tc_smem);
   float* Tb[6];
