@@ -164,10 +164,14 @@ struct ApplyShape {
 };
 
 // T: arithmetic and table type; TIO: type of u, f, v in global memory.
-template <typename T, int DIM, int NP, bool RESIDUAL, typename TIO = T>
+// NPC > 0 (with RESIDUAL): the residual is not stored but restricted at once,
+// fc = (J (x) J (x) J)^T (f - A u) element by element (Sec. 3.2; J is NP x NPC,
+// row-major), in the operation order of the separate restriction kernel.
+template <typename T, int DIM, int NP, bool RESIDUAL, typename TIO = T, int NPC = 0>
 __global__ void __launch_bounds__(ApplyShape<DIM, NP>::THREADS, sizeof(T) == 8 ? ApplyShape<DIM, NP>::MINB8 : 0)
 apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const TIO* __restrict__ f,
-             TIO* __restrict__ v) {
+             TIO* __restrict__ v, const T* __restrict__ J = nullptr, TIO* __restrict__ fc = nullptr) {
+  static_assert(NPC == 0 || (RESIDUAL && NPC < NP), "fused restriction: residual, coarser order");
   using S = ApplyShape<DIM, NP>;
   constexpr int P = NP - 1;
   extern __shared__ __align__(16) unsigned char apply_smem[];
@@ -234,7 +238,10 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
   // v = (M_z (x) M_y (x) M_x) * (sum over axes of M_d^-1 L_d u)
   for (int t = tid; t < nodes_blk; t += blockDim.x) {
     long long g = e0 * S::NODES + t;
-    if (g >= total) continue;
+    if (g >= total) {
+      if constexpr (NPC > 0) acc[t] = T(0);
+      continue;
+    }
     const int le = t / S::NODES;
     const int nd = t - le * S::NODES;
     const int i = nd % NP, j = (nd / NP) % NP;
@@ -246,7 +253,50 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
       m = m * ldg(at.M[2] + (size_t)mz * NP + k);
     }
     const T val = m * acc[t];
-    v[g] = RESIDUAL ? TIO(T(f[g]) - val) : TIO(val);
+    if constexpr (NPC > 0) acc[t] = T(f[g]) - val;
+    else v[g] = RESIDUAL ? TIO(T(f[g]) - val) : TIO(val);
+  }
+  if constexpr (NPC > 0) {
+    // restriction of the element residuals (in acc): x, y and z passes with J^T
+    constexpr int NZF = (DIM == 3) ? NP : 1;
+    constexpr int B1 = NPC * NP * NZF, B2 = NPC * NPC * NZF;
+    __syncthreads();
+    T* b1 = su;                                  // staged u is no longer needed
+    for (int t = tid; t < S::EPB * B1; t += blockDim.x) {
+      const int le = t / B1, tt = t - le * B1;
+      const int o = tt % NPC, rest = tt / NPC;
+      const T* rr = acc + le * S::NODES + rest * NP;
+      T sum = T(0);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) sum = madd(ldg(J + a * NPC + o), rr[a], sum);
+      b1[le * B1 + tt] = sum;
+    }
+    __syncthreads();
+    T* b2 = acc;
+    for (int t = tid; t < S::EPB * B2; t += blockDim.x) {
+      const int le = t / B2, tt = t - le * B2;
+      const int i = tt % NPC, o = (tt / NPC) % NPC, c = tt / (NPC * NPC);
+      T sum = T(0);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) sum = madd(ldg(J + a * NPC + o), b1[le * B1 + (c * NP + a) * NPC + i], sum);
+      if (DIM == 2) {
+        if (e0 + le < dm.nelem) fc[(e0 + le) * B2 + tt] = TIO(sum);
+      } else {
+        b2[le * B2 + tt] = sum;
+      }
+    }
+    if (DIM == 3) {
+      __syncthreads();
+      constexpr int NC3 = NPC * NPC * NPC;
+      for (int t = tid; t < S::EPB * NC3; t += blockDim.x) {
+        const int le = t / NC3, tt = t - le * NC3;
+        const int ij = tt % (NPC * NPC), o = tt / (NPC * NPC);
+        T sum = T(0);
+#pragma unroll
+        for (int a = 0; a < NP; ++a) sum = madd(ldg(J + a * NPC + o), b2[le * B2 + a * NPC * NPC + ij], sum);
+        if (e0 + le < dm.nelem) fc[(e0 + le) * NC3 + tt] = TIO(sum);
+      }
+    }
   }
 }
 
@@ -321,6 +371,20 @@ static int apply_dispatch(const LevelDims& dm, const ApplyTables<T>& at, const T
     if (!set_smem(apply_kernel<T, DIM, NP, false, TIO>, smem)) return PMG_ECUDA;
     count_launch(); apply_kernel<T, DIM, NP, false, TIO><<<(unsigned)blocks, S::THREADS, smem, s>>>(dm, at, u, f, v);
   }
+  return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
+}
+
+// v-less residual + restriction: fc = I^T (f - A u) for the staged kernel's shapes;
+// PMG_EINVAL where no fused kernel exists (the caller then runs the two kernels).
+template <typename T, int DIM, int NP, int NPC>
+static int residual_restrict_dispatch(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f,
+                                      const T* J, T* fc, cudaStream_t s) {
+  using S = ApplyShape<DIM, NP>;
+  long long blocks = (dm.nelem + S::EPB - 1) / S::EPB;
+  const size_t smem = 2 * sizeof(T) * S::EPB * S::NODES;
+  if (!set_smem(apply_kernel<T, DIM, NP, true, T, NPC>, smem)) return PMG_ECUDA;
+  count_launch();
+  apply_kernel<T, DIM, NP, true, T, NPC><<<(unsigned)blocks, S::THREADS, smem, s>>>(dm, at, u, f, nullptr, J, fc);
   return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
 }
 

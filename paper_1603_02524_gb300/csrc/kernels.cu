@@ -26,6 +26,24 @@ int launch_apply(const LevelDims& dm, const ApplyTables<T>& at, const T* u, cons
 #undef PMG_APPLY_CASE
   return PMG_EINVAL;
 }
+// fc = I^T (f - A u) in one kernel (the residual is not stored); PMG_EINVAL for
+// shapes without the fused kernel (3-D P = 32), where the caller runs the two.
+template <typename T>
+int launch_residual_restrict(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f,
+                             const T* J, T* fc, cudaStream_t s) {
+  if (dm.nelem == 0) return PMG_OK;
+#define PMG_RR_CASE(DIMV, NPV, NPCV) \
+  if (dm.dim == DIMV && dm.NP == NPV) return residual_restrict_dispatch<T, DIMV, NPV, NPCV>(dm, at, u, f, J, fc, s);
+  PMG_RR_CASE(3, 3, 2) PMG_RR_CASE(3, 5, 3) PMG_RR_CASE(3, 9, 5) PMG_RR_CASE(3, 17, 9)
+  PMG_RR_CASE(2, 3, 2) PMG_RR_CASE(2, 5, 3) PMG_RR_CASE(2, 9, 5) PMG_RR_CASE(2, 17, 9) PMG_RR_CASE(2, 33, 17)
+#undef PMG_RR_CASE
+  return PMG_EINVAL;
+}
+template int launch_residual_restrict<double>(const LevelDims&, const ApplyTables<double>&, const double*,
+                                              const double*, const double*, double*, cudaStream_t);
+template int launch_residual_restrict<float>(const LevelDims&, const ApplyTables<float>&, const float*,
+                                             const float*, const float*, float*, cudaStream_t);
+
 template int launch_apply<double>(const LevelDims&, const ApplyTables<double>&, const double*,
                                   const double*, double*, cudaStream_t);
 template int launch_apply<float>(const LevelDims&, const ApplyTables<float>&, const float*,

@@ -240,6 +240,9 @@ template <typename T>
 int launch_apply(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f, T* v,
                  cudaStream_t s);
 template <typename T>
+int launch_residual_restrict(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f,
+                             const T* J, T* fc, cudaStream_t s);
+template <typename T>
 int launch_fdm(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, cudaStream_t s);
 template <typename T>
 int launch_restrict(const LevelDims& fine, const LevelDims& coarse, const T* J, const T* rf, T* fc,

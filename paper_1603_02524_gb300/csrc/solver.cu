@@ -383,10 +383,16 @@ void vcycle(Hier& h, const T* fL, T* uL, cudaStream_t s) {
     LevelDev<T>& d = lev<T>(h, l);
     PMG_CUDA(cudaMemsetAsync(u[l], 0, sizeof(T) * h.dims[l].ndof, s));
     smooth_level<T>(h, l, u[l], f[l], ns_level(h, l, false), true, s);
-    PMG_CHECK(launch_apply<T>(h.dims[l], d.at, u[l], f[l], d.r, s));
     T* J = nullptr;
     if constexpr (sizeof(T) == 8) J = (T*)h.J64[l]; else J = (T*)h.J32[l];
-    PMG_CHECK(launch_restrict<T>(h.dims[l], h.dims[l - 1], J, d.r, lev<T>(h, l - 1).f, s));
+    // f_{l-1} = I^T (f_l - A u_l): one fused kernel, else residual and restriction apart
+    const int rr = launch_residual_restrict<T>(h.dims[l], d.at, u[l], f[l], J, lev<T>(h, l - 1).f, s);
+    if (rr == PMG_EINVAL) {
+      PMG_CHECK(launch_apply<T>(h.dims[l], d.at, u[l], f[l], d.r, s));
+      PMG_CHECK(launch_restrict<T>(h.dims[l], h.dims[l - 1], J, d.r, lev<T>(h, l - 1).f, s));
+    } else {
+      PMG_CHECK(rr);
+    }
   }
   // coarse grid solution in fp64 (Algorithm 1, A_0^+ f_0)
   if constexpr (sizeof(T) == 8) {
