@@ -77,15 +77,39 @@ static bool set_smem(K fn, size_t bytes) {
 // the element, values x): the element's own block L^0 (even-odd form when the block
 // is centro-symmetric), plus the neighbour blocks L^-, L^+ from the adjacent lines
 // in global u.
+// The tables of axis d, selected with compile-time indices (a runtime index into
+// the kernel-parameter arrays would copy them to local memory).
+template <typename T>
+struct ApplyAxis {
+  const T* L0;
+  const int* sym;
+  const T* cpl;
+  int m;              // element index along the axis
+  int ned;            // elements along the axis
+  long long estride;  // element stride of the axis
+};
+template <typename T>
+__device__ __forceinline__ ApplyAxis<T> apply_axis(const LevelDims& dm, const ApplyTables<T>& at,
+                                                   const int (&me)[3], int d) {
+  ApplyAxis<T> a;
+  a.L0 = d == 0 ? at.L0[0] : (d == 1 ? at.L0[1] : at.L0[2]);
+  a.sym = d == 0 ? at.sym[0] : (d == 1 ? at.sym[1] : at.sym[2]);
+  a.cpl = d == 0 ? at.cpl[0] : (d == 1 ? at.cpl[1] : at.cpl[2]);
+  a.m = d == 0 ? me[0] : (d == 1 ? me[1] : me[2]);
+  a.ned = d == 0 ? dm.ne[0] : (d == 1 ? dm.ne[1] : dm.ne[2]);
+  a.estride = (d == 0) ? 1 : (d == 1 ? (long long)dm.ne[0] : (long long)dm.ne[0] * dm.ne[1]);
+  return a;
+}
+
 template <typename T, int NP, int NODES, typename TIO>
-__device__ __forceinline__ void apply_line(const LevelDims& dm, const ApplyTables<T>& at,
-                                           const TIO* __restrict__ u, long long e, const int (&me)[3],
-                                           int d, int off, int stride, const T (&x)[NP], T (&y)[NP]) {
+__device__ __forceinline__ void apply_line(const ApplyTables<T>& at, const ApplyAxis<T>& ax,
+                                           const TIO* __restrict__ u, long long e, int off, int stride,
+                                           const T (&x)[NP], T (&y)[NP]) {
   constexpr int P = NP - 1;
   constexpr int H = NP / 2, NE = NP - H, NO = H;
   constexpr int PNP = apad<T>(NP);
-  const T* L0 = at.L0[d] + (size_t)me[d] * NP * PNP;
-  if (__ldg(at.sym[d] + me[d])) {
+  const T* L0 = ax.L0 + (size_t)ax.m * NP * PNP;
+  if (__ldg(ax.sym + ax.m)) {
     // even-odd split of the centro-symmetric block (folded, transposed rows)
     constexpr int PE = apad<T>(NE), PO = apad<T>(NO > 0 ? NO : 1);
     T xp[NE], xm[NO > 0 ? NO : 1];
@@ -120,11 +144,11 @@ __device__ __forceinline__ void apply_line(const LevelDims& dm, const ApplyTable
     for (int a = 0; a < NP; ++a) apply_axpy<T, NP>(y, L0 + a * PNP, x[a]);
   }
   // neighbour blocks L^-, L^+ (rank <= 3, already scaled by M_d^-1)
-  const T* c = at.cpl[d] + (size_t)me[d] * (2 * PNP + 8);
-  const long long estride = (d == 0) ? 1 : (d == 1 ? (long long)dm.ne[0] : (long long)dm.ne[0] * dm.ne[1]);
-  const int ned = dm.ne[d];
+  const T* c = ax.cpl + (size_t)ax.m * (2 * PNP + 8);
+  const long long estride = ax.estride;
+  const int ned = ax.ned;
   if (ldg(c + 2 * PNP + 2) != T(0)) {          // neighbour m-1 exists
-    long long en = (me[d] > 0) ? e - estride : e + (long long)(ned - 1) * estride;
+    long long en = (ax.m > 0) ? e - estride : e + (long long)(ned - 1) * estride;
     const TIO* un = u + en * NODES + off;
     T uP = T(0), dP = T(0);
 #pragma unroll
@@ -137,7 +161,7 @@ __device__ __forceinline__ void apply_line(const LevelDims& dm, const ApplyTable
     y[0] += ldg(c + 2 * PNP + 0) * dP - ldg(c + 2 * PNP + 1) * uP;
   }
   if (ldg(c + 2 * PNP + 5) != T(0)) {          // neighbour m+1 exists
-    long long en = (me[d] < ned - 1) ? e + estride : e - (long long)(ned - 1) * estride;
+    long long en = (ax.m < ned - 1) ? e + estride : e - (long long)(ned - 1) * estride;
     const TIO* un = u + en * NODES + off;
     T u0 = T(0), d0 = T(0);
 #pragma unroll
@@ -226,7 +250,7 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
       T x[NP], y[NP];
 #pragma unroll
       for (int a = 0; a < NP; ++a) x[a] = sel[off + a * stride];
-      apply_line<T, NP, S::NODES, TIO>(dm, at, u, e, me, d, off, stride, x, y);
+      apply_line<T, NP, S::NODES, TIO>(at, apply_axis(dm, at, me, d), u, e, off, stride, x, y);
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
         if (d == 0) ael[off + i * stride] = y[i];
@@ -325,7 +349,7 @@ apply_axis_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u,
   T x[NP], y[NP];
 #pragma unroll
   for (int a = 0; a < NP; ++a) x[a] = T(ue[off + a * stride]);
-  apply_line<T, NP, NODES, TIO>(dm, at, u, e, me, d, off, stride, x, y);
+  apply_line<T, NP, NODES, TIO>(at, apply_axis(dm, at, me, d), u, e, off, stride, x, y);
   if (d == 0) {
 #pragma unroll
     for (int i = 0; i < NP; ++i) ve[off + i * stride] = TIO(y[i]);
