@@ -42,7 +42,8 @@ class Hierarchy:
     """p-multigrid hierarchy (Sec. 3.2).
 
     smoother: 'EA' | 'FA' | 'EM' | 'FM'; overlap '0' | 'l'; weighting as in Smoother.
-    ns: (pre, post) steps; variable=True -> n_{s,l} = ns * 2^(L-l) (variable V-cycle).
+    ns: (pre, post) steps; variable=True -> n_{s,l} = ns * 2^(L-l) (variable V-cycle of
+    Sec. 4.3, pinned by the face-centred columns of Table 4).
     coarse: 'cg' (the paper's choice) or 'dense' (pseudo-inverse, tiny grids only).
     """
 

@@ -68,35 +68,65 @@ def _golden_rows():
         line = line.strip()
         if not line or line.startswith("#"):
             continue
-        src, meth, sm, P, n, rbar, n10 = line.split()
-        rows.append((src, meth, sm, int(P), int(n), float(rbar), None if n10 == "-" else int(n10)))
+        src, meth, sm, P, n, beta, ar, cyc, rbar, n10 = line.split()
+        rows.append((src, meth, sm, int(P), int(n), float(beta), int(ar), cyc, float(rbar),
+                     None if n10 == "-" else int(n10)))
     return rows
 
 
-def _paper_run(meth, sm, P, n):
+def _paper_hierarchy(sm, P, n, beta=0.0, aspect=1, variable=False):
     kind, ov = sm[:2], sm[2:]
-    # Table 3 shows the rates are h-independent: its 8 x 8 rows are run as printed;
-    # Table 2 (16 x 16) rows run on the printed grid
-    w = syn.paper_periodic_2d(n, P)
-    h = Hierarchy(2, P, w.spacing, True, smoother=kind, overlap=ov, weighting="quintic")
+    w = syn.paper_periodic_2d(n, P, aspect=aspect, beta=beta)
+    h = Hierarchy(2, P, w.spacing, True, beta=beta, smoother=kind, overlap=ov, weighting="quintic",
+                  variable=variable)
+    return w, h
+
+
+def _paper_run(meth, w, h):
+    from oracle.layout import to_global
     d = h.fine
     F = d.rhs(d.nodal(syn.sin_source(2)))
     F -= F.mean()
-    U0 = syn.unit_uniform(w, seed=1)
-    from oracle.layout import to_global
-    U0 = to_global(U0, 2)
+    U0 = to_global(syn.unit_uniform(w, seed=1), 2)
     U, hist = (mgcg if meth == "MGCG" else mg)(h, U0, F, rtol=1e-10, maxit=150)
     return rates(hist)
 
 
-@pytest.mark.parametrize("row", _golden_rows(), ids=lambda r: f"{r[0]}-{r[1]}-{r[2]}-P{r[3]}")
+def _row_id(r):
+    src, meth, sm, P, n, beta, ar, cyc = r[:8]
+    return f"{src}-{meth}-{sm}-P{P}-n{n}" + (f"-b{beta}" if beta else "") + (f"-AR{ar}" if ar != 1 else "") \
+        + ("-varV" if cyc == "VV" else "")
+
+
+@pytest.mark.parametrize("row", _golden_rows(), ids=_row_id)
 def test_paper_convergence_rates(row):
-    """Tables 2 and 3 (Sec. 4.3): n10 within +-1 and rbar within 15 %."""
-    src, meth, sm, P, n, rbar, n10 = row
-    got = _paper_run(meth, sm, P, n)
+    """Tables 2, 3 and 4 (Sec. 4.3): n10 within +-1 and rbar within 15 %.  Table 3 shows the
+    rates are h-independent; its 8 x 8 rows run as printed, Tables 2 and 4 on 16 x 16."""
+    src, meth, sm, P, n, beta, ar, cyc, rbar, n10 = row
+    w, h = _paper_hierarchy(sm, P, n, beta, ar, variable=(cyc == "VV"))
+    got = _paper_run(meth, w, h)
     assert abs(got["rbar"] - rbar) <= 0.15 * rbar, got
     if n10 is not None:
         assert got["n10"] is not None and abs(got["n10"] - n10) <= 1, got
+
+
+@pytest.mark.parametrize("mistake", ["reversed", "fixed"])
+def test_variable_vcycle_pin_catches_a_wrong_schedule(mistake):
+    """Plants a plausible mistake in the oracle's variable V-cycle (Table 4, FA_0, P = 4,
+    AR = 16, printed n10 = 34): the smoothing steps doubled towards the FINE levels,
+    n_{s,l} = 2^(l-1), or not doubled at all.  The Table 4 pin (n10 within +-1) must reject
+    both, while the correct schedule n_{s,l} = 2^(L-l) passes."""
+    w, h = _paper_hierarchy("FA0", 4, 16, aspect=16, variable=True)
+    assert [lev.ns for lev in h.levels] == [(0, 0), (2, 2), (1, 1)]
+    if mistake == "reversed":
+        good = _paper_run("MGCG", w, h)
+        assert abs(good["n10"] - 34) <= 1
+    for l, lev in enumerate(h.levels):
+        if l > 0:
+            k = 2 ** (l - 1) if mistake == "reversed" else 1
+            lev.ns = (k, k)
+    bad = _paper_run("MGCG", w, h)
+    assert abs(bad["n10"] - 34) > 1, bad
 
 
 def test_printed_overlap_formula_misses_table3_at_P4():
