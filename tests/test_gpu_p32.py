@@ -3,8 +3,8 @@
 apply runs one launch per axis, the transfers between P = 32 and 16 share one
 in-place buffer, and the patch solves keep their patch buffer in global scratch.
 Tolerances as in test_gpu_parity.py (operator and transfers 1e-13, one Schwarz
-step 1e-11, MGCG solution 1e-9 with the oracle's iteration count; fp32 V-cycle
-steps 1e-4; double-float apply 1e-12).
+step 1e-11, MGCG solution 1e-10 with the oracle's iteration count; fp32 V-cycle
+steps 1e-4; double-float apply 1e-12; mixed + double-float solve 1e-9).
 """
 import numpy as np
 import pytest
@@ -109,7 +109,7 @@ def test_p32_mgcg(case):
         r = ref
         if per:
             got, r = got - got.mean(), ref - ref.mean()
-        assert rel_err(got, r) < 1e-9
+        assert rel_err(got, r) < 1e-10
     hm = make(case, precision="mixed", outer_apply="df")[1]
     hm.autotune()
     u = torch.zeros(int(np.prod(shape)), dtype=torch.float64, device="cuda")

@@ -5,7 +5,7 @@ FP64 mode tolerances (relative to the max-norm of the oracle result):
   one Schwarz step                       1e-11  (eigen-tables from two different
                                                  eigen-solvers; kappa(L_s) ~ 1e4-1e6)
   coarse solve, V-cycle                  1e-10
-  full MGCG solve (rtol 1e-10)           1e-9 of the solution, equal iteration counts
+  full MGCG solve (rtol 1e-10)           1e-10 of the solution, equal iteration counts
 """
 import numpy as np
 import pytest
@@ -195,7 +195,7 @@ def test_mgcg_solve(case, kind):
     got = from_dev(u, shape)
     if per:
         got, ref = got - got.mean(), ref - ref.mean()
-    assert rel_err(got, ref) < 1e-9
+    assert rel_err(got, ref) < 1e-10
 
 
 def test_config1_manufactured_solution():
@@ -217,7 +217,7 @@ def test_config1_manufactured_solution():
     U, ohist = mgcg(oh, np.zeros_like(F), F, rtol=1e-10)
     assert iters == len(ohist) - 1
     got = from_dev(u, elem_shape(2, w.n_elem, w.P))
-    assert rel_err(got, g2e(U, w.n_elem, w.P)) < 1e-9
+    assert rel_err(got, g2e(U, w.n_elem, w.P)) < 1e-10
     exact = g2e(d.nodal(syn.sin_solution(2)), w.n_elem, w.P)
     assert np.abs(got - exact).max() < 2e-3          # discretisation error at P = 4, h = 1/4
 
