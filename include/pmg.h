@@ -25,8 +25,12 @@
  *    iteration, later ones and batches once per call).
  *  - Every call returns a pmg_status (0 = PMG_OK) and never throws.  Invalid
  *    arguments are rejected before any work is enqueued.  Kernel launch errors
- *    return PMG_ECUDA; numerical breakdown detected on the device returns
- *    PMG_EBREAKDOWN / PMG_ENAN after the synchronisation of pmg_solve.
+ *    return PMG_ECUDA.  Conditions detected on the device (a non-finite residual,
+ *    CG breakdown, a bounded device wait that gave up) are written to the
+ *    hierarchy's device status word: pmg_solve / pmg_solve_host / pmg_batch_solve
+ *    stop the iteration and return them (PMG_ENAN, PMG_EBREAKDOWN, PMG_ETIMEOUT)
+ *    after their synchronisation; the asynchronous calls (pmg_smooth, pmg_vcycle,
+ *    pmg_schwarz_sweep) leave them there for pmg_device_status.
  *  - A hierarchy object is not thread safe: calls that use it must not run
  *    concurrently (they share its workspace).
  */
@@ -49,7 +53,8 @@ typedef enum {
   PMG_ENOCONV = -4,      /* pmg_solve: tolerance not reached within max_iter */
   PMG_EBREAKDOWN = -5,   /* pmg_solve: p^T A p <= 0 or delta <= 0 */
   PMG_ENAN = -6,         /* pmg_solve: non-finite residual */
-  PMG_ETIMEOUT = -7      /* reserved: a bounded device wait gave up */
+  PMG_ETIMEOUT = -7      /* a bounded device wait gave up (tcgen05 patch kernel, PMG_PREC_MIXED_TF32):
+                            the corrections of that sweep are incomplete */
 } pmg_status;
 
 /* Smoother (Sec. 3.1): additive element-centred (EA) or face-centred (FA). */
@@ -198,8 +203,10 @@ int pmg_coarse_solve(pmg_hier h, const double* f0_dev, double* u0_dev, void* str
  * counterpart; this is a library-integration entry point).  Same arguments,
  * same result as pmg_coarse_solve; the call allocates nothing.  Its two scratch
  * vectors live in a fixed 4 MiB device array compiled into the library, so it
- * suits callers that must not allocate while solving: code recorded into a CUDA
- * graph by stream capture, or code whose host framework owns all device memory.
+ * suits callers that cannot call cudaMalloc while they solve: code inside a host
+ * framework whose own allocator owns all device memory and forbids side
+ * allocations, or a caller that has reserved its memory up front and must not
+ * grow it mid-run.
  *  - Limit: the P = 1 problem may have at most 262 144 unknowns (32^3 elements in
  *    3-D); larger hierarchies get PMG_EINVAL and a message in pmg_last_error.
  *  - The first call on each device looks up the array's device address; make that
@@ -328,6 +335,16 @@ int pmg_schwarz_sweep_native(pmg_hier h, int level, int family, void* stream);
  * axes): the figure the benchmark's roofline uses.  Host only. */
 int pmg_schwarz_sweep_fma(pmg_hier h, int level, int family, double* fma);
 
+/* Benchmark hook (not part of the paper's method): enqueues on `stream` one launch
+ * of a multiply-add throughput probe on the FP64 (fp64 != 0) or FP32 pipes, every
+ * resident thread of every SM running independent multiply-add chains for `iters`
+ * loop trips, and stores in *flops the floating-point operations of that launch
+ * (2 per multiply-add).  Timing the launch with CUDA events on `stream` gives the
+ * measured peak that the roofline fractions of ALU-bound kernels divide by.
+ * Allocates nothing.  PMG_EINVAL for iters < 1 or a null flops, PMG_ECUDA on a
+ * launch error. */
+int pmg_fma_probe(int fp64, int iters, void* stream, double* flops);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all hierarchies, all devices); for counting launches in a timed region. */
 unsigned long long pmg_kernel_launches(void);
@@ -339,6 +356,29 @@ unsigned long long pmg_kernel_launches(void);
  * device.  Returns PMG_OK, or PMG_EINVAL for a null pointer, PMG_ECUDA on a CUDA
  * error. */
 int pmg_tc_timeouts(unsigned int* count);
+
+/*
+ * Device status word of a hierarchy (see the conventions at the top): enqueues its
+ * read on `stream`, synchronises that stream, stores the value in *status (PMG_OK,
+ * or PMG_ENAN / PMG_EBREAKDOWN / PMG_ETIMEOUT left by an earlier call on this
+ * hierarchy) and resets it to PMG_OK.  pmg_solve resets the word when it starts.
+ * Returns PMG_OK, PMG_EINVAL (null argument) or PMG_ECUDA.
+ */
+int pmg_device_status(pmg_hier h, void* stream, int* status);
+
+/*
+ * Test hook for the failure path of the bounded device waits (not part of the
+ * paper's method).  limit_us > 0: every block of this hierarchy's tcgen05 patch
+ * kernels (PMG_PREC_MIXED_TF32, 3-D patches of 13^3 nodes and more) waits after its
+ * first MMAs on an mbarrier that nothing completes, gives up after limit_us
+ * microseconds, lets its MMAs finish (bounded wait of about one second), frees its
+ * tensor memory and stops, counting itself in pmg_tc_timeouts and setting
+ * PMG_ETIMEOUT in the hierarchy's device status word; no fault, trap or unbounded
+ * wait is involved.  limit_us = 0 restores normal operation.  Captured graphs of
+ * the hierarchy are discarded (synchronises the device).  PMG_EINVAL for a null
+ * hierarchy or limit_us > 10^6.
+ */
+int pmg_test_stall_tc_waits(pmg_hier h, unsigned int limit_us);
 
 #ifdef __cplusplus
 }

@@ -29,7 +29,8 @@ EXPORTS = ["pmg_options_default", "pmg_grid_create", "pmg_grid_destroy", "pmg_gr
            "pmg_schwarz_sweep_fma", "pmg_schwarz_sweep_native", "pmg_mlp_forward",
            "pmg_mlp_backward", "pmg_mlp_adam", "pmg_batch_create", "pmg_batch_solve",
            "pmg_batch_destroy", "pmg_batch_last_error", "pmg_hierarchy_autotune", "pmg_tuned_threads",
-           "pmg_tc_timeouts"]
+           "pmg_tc_timeouts", "pmg_device_status", "pmg_test_stall_tc_waits",
+           "pmg_fma_probe"]
 
 
 class PmgOptions(ctypes.Structure):
@@ -91,6 +92,9 @@ def load(path: str | None = None):
         "pmg_schwarz_sweep": (i, [vp, i, i, vp, vp, vp]),
         "pmg_kernel_launches": (ctypes.c_ulonglong, []),
         "pmg_tc_timeouts": (i, [ctypes.POINTER(ctypes.c_uint)]),
+        "pmg_device_status": (i, [vp, vp, ctypes.POINTER(ctypes.c_int)]),
+        "pmg_test_stall_tc_waits": (i, [vp, ctypes.c_uint]),
+        "pmg_fma_probe": (i, [i, i, vp, ctypes.POINTER(ctypes.c_double)]),
         "pmg_coarse_solve_static": (i, [vp, vp, vp, vp]),
         "pmg_schwarz_sweep_fma": (i, [vp, i, i, ctypes.POINTER(ctypes.c_double)]),
         "pmg_schwarz_sweep_native": (i, [vp, i, i, vp]),
@@ -306,6 +310,18 @@ class Hierarchy:
         if rc not in (0, -4):
             _check("pmg_solve_host", rc, self.handle)
         return rc, st.iterations
+
+    def device_status(self, stream=None):
+        """Read and reset the hierarchy's device status word (pmg_device_status)."""
+        v = ctypes.c_int(0)
+        _check("pmg_device_status", load().pmg_device_status(self.handle, _stream(stream), ctypes.byref(v)),
+               self.handle)
+        return v.value
+
+    def test_stall_tc_waits(self, limit_us):
+        """Test hook: make the tcgen05 patch kernel's bounded waits run out (pmg_test_stall_tc_waits)."""
+        _check("pmg_test_stall_tc_waits", load().pmg_test_stall_tc_waits(self.handle, int(limit_us)),
+               self.handle)
 
     def autotune(self, stream=None):
         """Pick the patch kernel's CTA size per level by timing (pmg_hierarchy_autotune)."""

@@ -19,7 +19,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(BUILD, "libpmg.so")
 
 SOURCES = ["setup.cpp", "kernels.cu", "solver.cu", "fdm_inst_d3.cu", "fdm_inst_d2.cu",
-           "fdm_inst_f3.cu", "fdm_inst_f3tc.cu", "fdm_inst_f2.cu", "coarse_static.cu", "mlp.cu", "apply_df.cu"]
+           "fdm_inst_f3.cu", "fdm_inst_f3tc.cu", "fdm_inst_f2.cu", "coarse_static.cu", "mlp.cu", "apply_df.cu",
+           "peak_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

@@ -1,11 +1,11 @@
 // pmg_coarse_solve_static: the exact coarse solve of pmg_coarse_solve with its two
 // scratch vectors taken from a fixed device array instead of hierarchy workspace.
 //
-// For callers that may not allocate device memory when they solve: code that runs
-// while a CUDA stream is being captured into a graph (cudaMalloc is not permitted
-// during capture), or code that lives inside a host framework whose own allocator
-// owns all device memory and forbids side allocations.  The call itself allocates
-// nothing: no cudaMalloc, no cudaFree, no allocating library routine.
+// For callers that cannot call cudaMalloc when they solve: code that lives inside a
+// host framework whose own allocator owns all device memory and forbids side
+// allocations, or a caller that reserved its memory up front and must not grow it
+// mid-run.  The call itself allocates nothing: no cudaMalloc, no cudaFree, no
+// allocating library routine.
 //
 // Limit: the coarse (P = 1) problem may have at most kCoarseStaticMaxDof = 262 144
 // unknowns (32^3 elements in 3-D).  The array, 2 x 262 144 doubles = 4 MiB, is part
@@ -78,6 +78,11 @@ extern "C" int pmg_coarse_solve_static(pmg_hier hh, const double* f0, double* u0
   c.tmp[0] = scratch;
   c.tmp[1] = scratch + kCoarseStaticMaxDof;
   rc = launch_coarse_fdm(h->dims[0], c, f0, u0, (cudaStream_t)stream);
-  if (rc != PMG_OK) h->err = "pmg_coarse_solve_static: kernel launch failed";
+  if (rc != PMG_OK) {
+    // take the launch error out of the runtime's sticky slot, so that a later call
+    // does not report it as its own
+    const cudaError_t e = cudaGetLastError();
+    h->err = std::string("pmg_coarse_solve_static: kernel launch failed: ") + cudaGetErrorString(e);
+  }
   return rc;
 }

@@ -10,9 +10,20 @@ namespace pmg {
 // CTAs of the tcgen05 kernel that gave up waiting for their MMAs (stays 0).
 __device__ unsigned int g_tc_timeouts;
 
+// Device address of g_tc_timeouts on the current device (looked up once per device).
 unsigned int* tc_timeouts_ptr() {
-  static unsigned int* p = nullptr;
-  if (!p && cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_tc_timeouts) != cudaSuccess) p = nullptr;
+  static PerDevice<unsigned int*> addr;
+  unsigned int* p = nullptr;
+  addr.with(
+      [](unsigned int*& a, int) {
+        return cudaGetSymbolAddress(reinterpret_cast<void**>(&a), g_tc_timeouts) == cudaSuccess && a
+                   ? (int)PMG_OK
+                   : (int)PMG_ECUDA;
+      },
+      [&](unsigned int*& a) {
+        p = a;
+        return (int)PMG_OK;
+      });
   return p;
 }
 

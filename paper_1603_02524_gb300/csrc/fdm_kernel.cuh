@@ -746,27 +746,36 @@ int fdm_launch(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, c
   if constexpr (fdm_pipelined<T, NA, NB, NC, TC>()) if (pipe) {
     constexpr size_t smem2 = 2 * PipeStage<T, NA, NB, NC>::BYTES;
     constexpr int maxt = fdm_max_threads<T, NA, NB, NC>();
-    static bool attr2 = false;
-    static int nsm = 0;
-    static int per_sm[maxt / 32 + 1] = {};
-    if (!attr2) {
-      if (smem2 > 48 * 1024 &&
-          cudaFuncSetAttribute(fdm_kernel_pipe<T, NA, NB, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem2) != cudaSuccess)
-        return PMG_ECUDA;
-      int dev = 0;
-      if (cudaGetDevice(&dev) != cudaSuccess ||
-          cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return PMG_ECUDA;
-      attr2 = true;
-    }
-    if (fam.count_total <= 0) return PMG_OK;
+    struct Shape {
+      int nsm;
+      int per_sm[maxt / 32 + 1];
+    };
+    static PerDevice<Shape> shapes;
     int threads = (fam.threads >= 32 && fam.threads % 32 == 0) ? fam.threads : fdm_threads<NA, NB, NC>();
     if (threads > maxt) threads = maxt;
-    int& occ = per_sm[threads / 32];
-    if (occ <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fdm_kernel_pipe<T, NA, NB, NC>, threads,
-                                                                  smem2) != cudaSuccess)
-      return PMG_ECUDA;
+    int occ = 0, nsm = 0;
+    const int rc = shapes.with(
+        [](Shape& sh, int dev) {
+          if (smem2 > 48 * 1024 &&
+              cudaFuncSetAttribute(fdm_kernel_pipe<T, NA, NB, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem2) != cudaSuccess)
+            return (int)PMG_ECUDA;
+          if (cudaDeviceGetAttribute(&sh.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return (int)PMG_ECUDA;
+          for (int& v : sh.per_sm) v = 0;
+          return (int)PMG_OK;
+        },
+        [&](Shape& sh) {
+          int& o = sh.per_sm[threads / 32];
+          if (o <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fdm_kernel_pipe<T, NA, NB, NC>, threads,
+                                                                      smem2) != cudaSuccess)
+            return (int)PMG_ECUDA;
+          occ = o;
+          nsm = sh.nsm;
+          return (int)PMG_OK;
+        });
+    if (rc != PMG_OK) return rc;
+    if (fam.count_total <= 0) return PMG_OK;
     long long grid = (long long)(occ > 0 ? occ : 1) * nsm;
     if (grid > fam.count_total) grid = fam.count_total;
     count_launch();
@@ -779,13 +788,10 @@ int fdm_launch(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, c
     static_assert(smem_g <= 227 * 1024, "patch tables do not fit in shared memory");
     if (!fam.scratch || fam.scratch_ctas <= 0 || fam.scratch_stride < (long long)NA * NB * NC)
       return PMG_EINVAL;
-    static bool attr_g = false;
-    if (!attr_g && smem_g > 48 * 1024) {
-      if (cudaFuncSetAttribute(fdm_kernel_gbuf<T, NA, NB, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem_g) != cudaSuccess)
-        return PMG_ECUDA;
-    }
-    attr_g = true;
+    if (smem_g > 48 * 1024 &&
+        cudaFuncSetAttribute(fdm_kernel_gbuf<T, NA, NB, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_g) != cudaSuccess)
+      return PMG_ECUDA;
     if (fam.count_total <= 0) return PMG_OK;
     int threads = (fam.threads >= 32 && fam.threads % 32 == 0) ? fam.threads : 256;
     if (threads > 256) threads = 256;
@@ -796,13 +802,10 @@ int fdm_launch(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, c
   } else {
   constexpr size_t smem = fdm_smem_bytes<T, NA, NB, NC, TC>();
   static_assert(smem <= 227 * 1024, "patch does not fit in shared memory");
-  static bool attr_done = false;
-  if (!attr_done && smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(fdm_kernel<T, NA, NB, NC, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return PMG_ECUDA;
-  }
-  attr_done = true;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(fdm_kernel<T, NA, NB, NC, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return PMG_ECUDA;
   if (fam.count_total <= 0) return PMG_OK;
   constexpr int maxt = fdm_max_threads<T, NA, NB, NC>();
   int threads = (fam.threads >= 32 && fam.threads % 32 == 0) ? fam.threads : fdm_threads<NA, NB, NC>();

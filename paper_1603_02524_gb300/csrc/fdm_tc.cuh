@@ -76,8 +76,10 @@ struct TcGeom {
   static constexpr int NOFF = (NA + NB + NC + 1) / 2 * 2;
   static constexpr uint32_t ROW_OFF = OFF_OFF + 8u * NOFF;
   static constexpr uint32_t LAM_OFF = ROW_OFF + 8u * (uint32_t)((NB * NC + 1) / 2 * 2);
+  // mbarrier of the MMA completions (+0), tensor-memory address slot (+8), and a
+  // second mbarrier that nothing ever completes (+16): the stalled-wait test hook
   static constexpr uint32_t BAR_OFF = (LAM_OFF + 4u * (NA + NB + NC) + 15) / 16 * 16;
-  static constexpr uint32_t BYTES = BAR_OFF + 16;
+  static constexpr uint32_t BYTES = BAR_OFF + 32;
   __host__ __device__ static constexpr uint32_t cols(int n, int m) { return (uint32_t)mt(m) * (uint32_t)npd(n); }
   static constexpr uint32_t COLS_USED = mx(mx(cols(NA, M0), cols(NB, M1)), mx(cols(NC, M2), cols(NB, M4)));
   static constexpr uint32_t TCOLS = COLS_USED <= 32 ? 32 : COLS_USED <= 64 ? 64 : COLS_USED <= 128 ? 128 : 256;
@@ -122,9 +124,12 @@ __device__ __forceinline__ void tc_table_async(float* B, const float* __restrict
 }
 // One line pass: MMAs of all row tiles (one thread), wait, read-back into the
 // next operand.  Returns false (uniformly) if the MMAs did not complete in time.
+// stall_ns != 0 (test hook): the threads wait instead on `never`, an mbarrier that
+// nothing completes, and give up after stall_ns; the MMAs stay in flight on mbar.
 template <int NA, int NB, int NC, int PASS>
 __device__ __forceinline__ bool tc_pass(float* A, const float* B, uint64_t* mbar, uint32_t& phase, uint32_t tmem,
-                                        const float* la, const float* lb, const float* lc) {
+                                        const float* la, const float* lb, const float* lc, uint64_t* never,
+                                        uint32_t stall_ns) {
   using G = TcGeom<NA, NB, NC>;
   constexpr int q = (PASS == 0 || PASS == 5) ? 0 : (PASS == 1 || PASS == 4) ? 1 : 2;
   constexpr int n = q == 0 ? NA : q == 1 ? NB : NC;
@@ -151,7 +156,7 @@ __device__ __forceinline__ bool tc_pass(float* A, const float* B, uint64_t* mbar
                        bd + (uint64_t)((ks * 256) >> 4), idesc, ks > 0);
     umma::mma_commit(mbar);
   }
-  const bool ok = umma::mbar_wait(mbar, phase, 1000000000ull);
+  const bool ok = stall_ns ? umma::mbar_wait(never, 0, stall_ns) : umma::mbar_wait(mbar, phase, 1000000000ull);
   phase ^= 1u;
   if (__syncthreads_or(!ok)) return false;
   umma::fence_after_sync();
@@ -219,7 +224,9 @@ __device__ __forceinline__ bool tc_pass(float* A, const float* B, uint64_t* mbar
 }
 
 // Persistent CTAs (blockDim a multiple of 128, at most 512) walk over the patches of a family.
-// *timeouts counts CTAs that gave up waiting for their MMAs (they stop early).
+// *timeouts counts CTAs that gave up waiting for their MMAs (they stop early); such a
+// CTA also sets the family's device status word (fam.status, the hierarchy's) to
+// PMG_ETIMEOUT if it holds no other status.
 template <int NA, int NB, int NC>
 __global__ void __launch_bounds__(512)
 fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, float* __restrict__ u,
@@ -237,12 +244,15 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
   float* lc = lb + NB;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(tc_smem + G::BAR_OFF);
   uint32_t* slot = reinterpret_cast<uint32_t*>(tc_smem + G::BAR_OFF + 8);
+  uint64_t* never = reinterpret_cast<uint64_t*>(tc_smem + G::BAR_OFF + 16);
+  const uint32_t stall_ns = fam.stall_ns;
   const int tid = threadIdx.x;
 
   // operand pads must hold finite values (their products with the zero table pads vanish)
   for (int i = tid; i < (int)(G::OFF_OFF / 4); i += blockDim.x) A[i] = 0.0f;
   if (tid == 0) {
     umma::mbar_init(mbar, 1);
+    umma::mbar_init(never, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (tid < 32) {
@@ -343,12 +353,12 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
     prev[0] = pidx[0];
     prev[1] = pidx[1];
     prev[2] = pidx[2];
-    ok = tc_pass<NA, NB, NC, 0>(A, Tb[0], mbar, phase, tmem, la, lb, lc) &&
-         tc_pass<NA, NB, NC, 1>(A, Tb[2], mbar, phase, tmem, la, lb, lc) &&
-         tc_pass<NA, NB, NC, 2>(A, Tb[4], mbar, phase, tmem, la, lb, lc) &&
-         tc_pass<NA, NB, NC, 3>(A, Tb[5], mbar, phase, tmem, la, lb, lc) &&
-         tc_pass<NA, NB, NC, 4>(A, Tb[3], mbar, phase, tmem, la, lb, lc) &&
-         tc_pass<NA, NB, NC, 5>(A, Tb[1], mbar, phase, tmem, la, lb, lc);
+    ok = tc_pass<NA, NB, NC, 0>(A, Tb[0], mbar, phase, tmem, la, lb, lc, never, stall_ns) &&
+         tc_pass<NA, NB, NC, 1>(A, Tb[2], mbar, phase, tmem, la, lb, lc, never, stall_ns) &&
+         tc_pass<NA, NB, NC, 2>(A, Tb[4], mbar, phase, tmem, la, lb, lc, never, stall_ns) &&
+         tc_pass<NA, NB, NC, 3>(A, Tb[5], mbar, phase, tmem, la, lb, lc, never, stall_ns) &&
+         tc_pass<NA, NB, NC, 4>(A, Tb[3], mbar, phase, tmem, la, lb, lc, never, stall_ns) &&
+         tc_pass<NA, NB, NC, 5>(A, Tb[1], mbar, phase, tmem, la, lb, lc, never, stall_ns);
     if (!ok) break;
     __syncthreads();
     {
@@ -375,7 +385,10 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
     __syncthreads();                             // staging, offsets and tables are rewritten next
   }
   if (!ok) {
-    if (tid == 0) atomicAdd(timeouts, 1u);
+    if (tid == 0) {
+      atomicAdd(timeouts, 1u);
+      if (fam.status) atomicCAS(fam.status, 0, (int)PMG_ETIMEOUT);
+    }
     // the MMAs may still be running: give them a bounded time before the release
     umma::mbar_wait(mbar, phase ^ 1u, 1000000000ull);
   }
@@ -392,46 +405,55 @@ int fdm_launch_tc(const LevelDims& dm, const FdmFamily<float>& fam, const float*
   using G = TcGeom<NA, NB, NC>;
   constexpr size_t smem = G::BYTES;
   static_assert(smem <= 227 * 1024, "tensor-core patch kernel: shared memory");
-  static bool init = false;
-  static int nsm = 0, occ[5] = {0, 0, 0, 0, 0};
-  static cudaFuncAttributes fa{};
-  static int smem_sm = 0, smem_rsv = 0, regs_sm = 0, thr_sm = 0, blk_sm = 0;
+  struct Shape {
+    int nsm, smem_sm, smem_rsv, regs_sm, thr_sm, blk_sm, numRegs;
+    int occ[5];
+  };
+  static PerDevice<Shape> shapes;
   const int threads = fam.threads >= 128 && fam.threads <= 512 && fam.threads % 128 == 0
                           ? fam.threads
                           : (G::NN >= 4096 ? 256 : 128);
-  if (!init) {
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(fdm_kernel_tc<NA, NB, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-      return PMG_ECUDA;
-    if (cudaFuncSetAttribute(fdm_kernel_tc<NA, NB, NC>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
-      return PMG_ECUDA;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, fdm_kernel_tc<NA, NB, NC>) != cudaSuccess)
-      return PMG_ECUDA;
-    init = true;
-  }
-  // resident CTAs per SM: shared memory, registers (whole warps, 256-register
-  // granules), threads, blocks, and the 512 tensor-memory columns
-  int& o = occ[threads / 128];
-  if (o <= 0) {
-    const int by_smem = smem_sm / ((int)smem + smem_rsv);
-    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
-    const int by_regs = regs_sm / (regs_warp * (threads / 32));
-    int v = by_smem < by_regs ? by_smem : by_regs;
-    if (v > thr_sm / threads) v = thr_sm / threads;
-    if (v > blk_sm) v = blk_sm;
-    if (v > 512 / (int)G::TCOLS) v = 512 / (int)G::TCOLS;
-    o = v < 1 ? 1 : v;
-  }
+  int o = 1, nsm = 0;
+  const int rc = shapes.with(
+      [](Shape& sh, int dev) {
+        cudaFuncAttributes fa{};
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(fdm_kernel_tc<NA, NB, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+          return (int)PMG_ECUDA;
+        if (cudaFuncSetAttribute(fdm_kernel_tc<NA, NB, NC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sh.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sh.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sh.smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sh.regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sh.thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sh.blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, fdm_kernel_tc<NA, NB, NC>) != cudaSuccess)
+          return (int)PMG_ECUDA;
+        sh.numRegs = fa.numRegs;
+        for (int& v : sh.occ) v = 0;
+        return (int)PMG_OK;
+      },
+      [&](Shape& sh) {
+        // resident CTAs per SM: shared memory, registers (whole warps, 256-register
+        // granules), threads, blocks, and the 512 tensor-memory columns
+        int& oc = sh.occ[threads / 128];
+        if (oc <= 0) {
+          const int by_smem = sh.smem_sm / ((int)smem + sh.smem_rsv);
+          const int regs_warp = (sh.numRegs * 32 + 255) / 256 * 256;
+          const int by_regs = sh.regs_sm / (regs_warp * (threads / 32));
+          int v = by_smem < by_regs ? by_smem : by_regs;
+          if (v > sh.thr_sm / threads) v = sh.thr_sm / threads;
+          if (v > sh.blk_sm) v = sh.blk_sm;
+          if (v > 512 / (int)G::TCOLS) v = 512 / (int)G::TCOLS;
+          oc = v < 1 ? 1 : v;
+        }
+        o = oc;
+        nsm = sh.nsm;
+        return (int)PMG_OK;
+      });
+  if (rc != PMG_OK) return rc;
   if (fam.count_total <= 0) return PMG_OK;
   long long grid = (long long)o * nsm;
   if (grid > fam.count_total) grid = fam.count_total;

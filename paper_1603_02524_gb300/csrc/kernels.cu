@@ -376,15 +376,23 @@ static int launch_coarse_split(const LevelDims& dm, const CoarseFdm& c, const do
 
 int launch_coarse_fdm(const LevelDims& dm, const CoarseFdm& c, const double* f, double* u,
                       cudaStream_t s, bool cooperative) {
-  static int per_sm = -1, nsm = 0;
-  if (per_sm < 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_fdm_fused_kernel, 256, 0) !=
-            cudaSuccess)
-      return PMG_ECUDA;
-  }
+  struct Shape { int per_sm, nsm; };
+  static PerDevice<Shape> shapes;
+  int per_sm = 0, nsm = 0;
+  const int rc = shapes.with(
+      [](Shape& sh, int dev) {
+        return (cudaDeviceGetAttribute(&sh.nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh.per_sm, coarse_fdm_fused_kernel, 256, 0) ==
+                    cudaSuccess)
+                   ? (int)PMG_OK
+                   : (int)PMG_ECUDA;
+      },
+      [&](Shape& sh) {
+        per_sm = sh.per_sm;
+        nsm = sh.nsm;
+        return (int)PMG_OK;
+      });
+  if (rc != PMG_OK) return rc;
   long long want = (dm.ndof + 255) / 256;
   long long cap = (long long)per_sm * nsm;
   int blocks = (int)(want < cap ? want : cap);
@@ -469,7 +477,7 @@ __device__ void finish_reduce(double a, double b, double* partial, unsigned* cou
   if (threadIdx.x == 0) {
     out[0] = sa;
     out[1] = sb;
-    if (check && status && !(sa == sa && sa < 1e300)) *status = PMG_ENAN;
+    if (check && status && *status == 0 && !(sa == sa && sa < 1e300)) *status = PMG_ENAN;
     *counter = 0u;
   }
 }
@@ -503,7 +511,7 @@ __global__ void cg_update_kernel(double* __restrict__ u, double* __restrict__ r,
   if (it_dev) save_old = *it_dev >= 2;
   const double pq = scal[S_PQ];
   const double alpha = scal[S_DELTA] / pq;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && status) {
+  if (blockIdx.x == 0 && threadIdx.x == 0 && status && *status == 0) {   // the first status stays
     if (!(pq > 0.0) || !(scal[S_DELTA] > 0.0)) *status = (pq == pq) ? PMG_EBREAKDOWN : PMG_ENAN;
   }
   double a = 0.0;
@@ -554,7 +562,8 @@ void launch_p_update(double* p, const double* z, const double* scal, int first, 
 // delta <- z.r (after the p update, which still needed the old delta)
 __global__ void set_delta_kernel(double* scal, int* status) {
   scal[S_DELTA] = scal[S_ZR];
-  if (status && !(scal[S_ZR] > 0.0)) *status = (scal[S_ZR] == scal[S_ZR]) ? PMG_EBREAKDOWN : PMG_ENAN;
+  if (status && *status == 0 && !(scal[S_ZR] > 0.0))
+    *status = (scal[S_ZR] == scal[S_ZR]) ? PMG_EBREAKDOWN : PMG_ENAN;
 }
 void launch_set_delta(double* scal, int* status, cudaStream_t s) {
   count_launch(); set_delta_kernel<<<1, 1, 0, s>>>(scal, status);

@@ -10,6 +10,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -25,6 +26,31 @@ extern std::atomic<unsigned long long> g_launches;
 inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 constexpr int kMaxLevels = 7;     // P <= 32 -> levels P_l = 1, 2, 4, ..., 32
+
+// Launch-shape figures (SM count, resident blocks, kernel attributes) kept per
+// device: a process may drive several GPUs, from several host threads.  with()
+// runs fn(entry) under the lock, after init(entry, device) has filled the current
+// device's entry on its first use; both return PMG_OK or an error status.
+constexpr int kMaxDevices = 64;
+template <typename T>
+struct PerDevice {
+  std::mutex mu;
+  T val[kMaxDevices];
+  bool ready[kMaxDevices] = {};
+  template <typename Init, typename Fn>
+  int with(Init&& init, Fn&& fn) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PMG_ECUDA;
+    if (dev < 0 || dev >= kMaxDevices) return PMG_EINVAL;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ready[dev]) {
+      const int rc = init(val[dev], dev);
+      if (rc != PMG_OK) return rc;
+      ready[dev] = true;
+    }
+    return fn(val[dev]);
+  }
+};
 
 // ---------------------------------------------------------------------------
 // host-side 1-D discretisation of one axis at one order (Sec. 2.4)
@@ -112,6 +138,12 @@ struct FdmFamily {
   const T* inv = nullptr;
   const int* uid[3] = {nullptr, nullptr, nullptr};
   int ucount[3] = {1, 1, 1};
+  // device status word of the owning hierarchy: the tcgen05 kernel sets PMG_ETIMEOUT
+  // there when a bounded wait gives up (null: counted only)
+  int* status = nullptr;
+  // test hook of the tcgen05 kernel (0 = off): its blocks wait on a barrier that
+  // nothing completes and give up after stall_ns nanoseconds
+  unsigned int stall_ns = 0;
 };
 
 struct LevelDims {

@@ -999,6 +999,12 @@ int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
     PMG_CUDA(cudaMemset(h->dstatus, 0, 4 * sizeof(int)));
     PMG_CUDA(cudaMemset(h->scal, 0, S_NUM * sizeof(double)));
     PMG_CUDA(cudaMallocHost(&h->hscal, sizeof(double) * (S_NUM + 2)));
+    // patch kernels that can detect a failed bounded wait report it in the hierarchy's
+    // status word, which pmg_solve reads (and pmg_device_status for the other calls)
+    for (int l = 1; l <= L; ++l) {
+      h->d32[l].ea.status = h->dstatus;
+      for (int q = 0; q < 3; ++q) h->d32[l].fa[q].status = h->dstatus;
+    }
     PMG_CUDA(cudaDeviceSynchronize());
     return PMG_OK;
   });
@@ -1294,6 +1300,43 @@ unsigned long long pmg_kernel_launches(void) { return g_launches.load(); }
 int pmg_tc_timeouts(unsigned int* count) {
   if (!count) return PMG_EINVAL;
   return tc_timeouts_take(count);
+}
+
+int pmg_device_status(pmg_hier hh, void* stream, int* status) {
+  Hier* h = H(hh);
+  if (!h || !status) return PMG_EINVAL;
+  return guarded(h, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    int v = 0;
+    PMG_CUDA(cudaMemcpyAsync(h->hscal + S_NUM, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PMG_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(&v, h->hscal + S_NUM, sizeof(int));
+    PMG_CUDA(cudaMemsetAsync(h->dstatus, 0, sizeof(int), s));
+    PMG_CUDA(cudaStreamSynchronize(s));
+    *status = v;
+    return (int)PMG_OK;
+  });
+}
+
+int pmg_test_stall_tc_waits(pmg_hier hh, unsigned int limit_us) {
+  Hier* h = H(hh);
+  if (!h || limit_us > 1000000u) return PMG_EINVAL;
+  const unsigned int ns = limit_us * 1000u;
+  for (int l = 1; l <= h->L; ++l) {
+    h->d32[l].ea.stall_ns = ns;
+    for (int q = 0; q < 3; ++q) h->d32[l].fa[q].stall_ns = ns;
+  }
+  // captured graphs hold the old kernel parameters: capture again on next use
+  return guarded(h, [&] {
+    PMG_CUDA(cudaDeviceSynchronize());
+    if (h->sv_exec) cudaGraphExecDestroy(h->sv_exec);
+    h->sv_exec = nullptr;
+    if (h->sv_state == 1) h->sv_state = 0;
+    if (h->pc_exec) cudaGraphExecDestroy(h->pc_exec);
+    h->pc_exec = nullptr;
+    if (h->pc_state == 1) h->pc_state = 0;
+    return (int)PMG_OK;
+  });
 }
 
 int pmg_schwarz_sweep_native(pmg_hier hh, int level, int family, void* stream) {

@@ -1,8 +1,8 @@
 """pmg_coarse_solve_static: the coarse solve that allocates nothing.
 
-Callers that may not allocate device memory while they solve (stream capture into
-a CUDA graph, or a host framework whose allocator owns all device memory) use this
-entry point; its scratch is a fixed array compiled into the library.  The test
+Callers that cannot call cudaMalloc while they solve (a host framework whose
+allocator owns all device memory, or a caller that reserved its memory up front)
+use this entry point; its scratch is a fixed array compiled into the library.  The test
 calls it through the C ABI twice in a row and checks each result against
 pmg_coarse_solve on the same hierarchy and input, then checks that a coarse
 problem above the stated limit is refused.
