@@ -1,16 +1,20 @@
 """Benchmark: DOF/s of the p-multigrid-preconditioned CG solve to a 1e-10 relative residual.
 
-Workload (default): 3-D Poisson on the unit cube, 16^3 uniform elements, P = 8
-(2 985 984 DOF), interior penalty (mu_star = 1), homogeneous Dirichlet walls,
+Workload (default): 3-D Poisson on the unit cube, 32^3 uniform elements, P = 16
+(160 989 184 DOF), interior penalty (mu_star = 1), homogeneous Dirichlet walls,
 f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z) + seeded U[-1, 1] nodal noise, MGCG with
 the element-centred additive Schwarz smoother (level-dependent overlap, quintic
 weights), V(1,1), u_0 = 0, FP64.  One step = one complete solve from u_0 = 0.
+`--workload c2` selects 16^3 elements at P = 8 (2 985 984 DOF), c4 the stretched
+64 x 16 x 8 grid, c5 the batch of 256 solves.
 
 The JSON line also reports the Schwarz patch kernel's own throughput and
-roofline fraction, the same solve with the mixed-precision V-cycle, the
-end-to-end number through the host-buffer C-ABI call, the FP64 CPU oracle timed
-on this host on a bounded sample, SM clocks during the timed region and the
-number of library kernels launched there.
+roofline fraction (against FP64 / FP32 multiply-add peaks measured in the same
+run by the library's probe kernel), the same solve in the other arithmetics
+(fp32 and tcgen05 tf32 V-cycles, double-float CG apply) with each solution's
+difference from the FP64 one, the end-to-end number through the host-buffer C-ABI
+call, the FP64 CPU oracle timed on this host on a bounded sample, SM clocks during
+the timed region and the number of library kernels launched there.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank solves its own replica (the solve does not
@@ -36,9 +40,6 @@ import synthetic as syn  # noqa: E402
 
 METRIC = "DOF/s to 1e-10 residual (MG-CG solve), smoother GDOF/s and % roofline, vs FP64 plain"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 / FP32 FMA throughput measured on this machine's GB300 (FMA-chain probe, 152 SMs, ~2.0 GHz)
-FP64_PEAK_GFLOPS = 1200.0
-FP32_PEAK_GFLOPS = 74800.0
 
 
 def _tf32_peak_gflops():
@@ -53,6 +54,13 @@ def _tf32_peak_gflops():
 
 TF32_PEAK_GFLOPS = _tf32_peak_gflops()
 
+# DRAM bytes (read + write) per patch of a patch-kernel version, from one ncu capture each
+# on a grid whose vectors exceed L2 (the summaries under profiles/); key: (arithmetic,
+# P, family, dim).  The roofline's `traffic` scales it by the bench grid's patch count.
+TRAFFIC_PER_PATCH = {
+    ("double", 8, "EA", 3): (383.47e6 + 162.46e6) / 32768,   # fdm_kernel<double,13,13,13>, 32^3 elements
+}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -60,7 +68,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2",
+    ap.add_argument("--workload", default="c3",
                     choices=["c1", "c2", "c2ldg", "c2x32", "c3", "c3s", "c4", "c5"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -86,7 +94,7 @@ DTYPE = {("fp64", "fp64"): "f64", ("mixed", "fp64"): "f64+f32", ("mixed_tc", "fp
          ("fp64", "df"): "f64+df32", ("mixed", "df"): "f64+df32+f32", ("mixed_tc", "df"): "f64+df32+f32(tf32x3)",
          ("mixed_tf32", "df"): "f64+df32+f32(tf32)"}
 # the solve's variants compared in the extras: label -> (V-cycle precision, outer apply)
-VARIANTS = {"fp64_plain": ("fp64", "fp64"), "mixed": ("mixed", "fp64"), "mixed_tc": ("mixed_tc", "fp64"),
+VARIANTS = {"fp64_plain": ("fp64", "fp64"), "mixed": ("mixed", "fp64"),
             "mixed_tf32": ("mixed_tf32", "fp64"), "mixed_df": ("mixed", "df"),
             "mixed_tf32_df": ("mixed_tf32", "df")}
 BATCH_OPTS = dict(smoother="FA", overlap="l", variable_v=True)
@@ -184,35 +192,65 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_baseline(w, opts, budget_s=30.0):
-    """The FP64 CPU oracle on a bounded sample of the workload: the same problem on 12^3
-    elements (or the full grid if smaller), complete MGCG solve to 1e-10."""
-    from oracle.layout import to_global
-    from oracle.mg import Hierarchy as OHier, mgcg
-    # about 1.2 M unknowns: 12^3 elements at P = 8, 6^3 at P = 16
-    side = max(2, round((1.2e6 / (w.P + 1) ** w.dim) ** (1.0 / w.dim)))
+def oracle_sample(w, target_dof=3.0e5):
+    """A bounded sample of the workload for the FP64 CPU oracle: the same problem on the
+    first k elements of each axis (k^3 elements with about target_dof unknowns; uniform
+    axes keep their length, so the element width grows), or the full grid if smaller."""
+    side = max(2, round((target_dof / (w.P + 1) ** w.dim) ** (1.0 / w.dim)))
     ne = tuple(min(n, side) for n in w.n_elem)
     sp = [list(s) if n == len(s) else (syn.uniform_spacing(n, float(sum(s))) if len(set(s)) == 1 else list(s[:n]))
           for n, s in zip(ne, w.spacing)]
-    sw = syn.Workload(w.name + "_sample", w.dim, w.P, ne, sp, w.periodic, w.beta, w.mu_star, w.rhs, w.seed)
-    t0 = time.perf_counter()
-    h = OHier(w.dim, w.P, sp, w.periodic, w.beta, w.mu_star, smoother=opts["smoother"],
-              overlap=opts["overlap"], variable=opts.get("variable_v", False))
-    d = h.fine
-    F = d.rhs(to_global(syn.source_values(sw, d.coords()), w.dim))
-    t1 = time.perf_counter()
-    U, hist = mgcg(h, np.zeros_like(F), F, rtol=1e-10)
-    t2 = time.perf_counter()
+    return syn.Workload(w.name + "_sample", w.dim, w.P, ne, sp, w.periodic, w.beta, w.mu_star, w.rhs, w.seed)
+
+
+def _cores():
     try:
-        cores = len(os.sched_getaffinity(0))
+        return len(os.sched_getaffinity(0))
     except AttributeError:
-        cores = os.cpu_count()
-    return {"value": d.ndof / (t2 - t1), "unit": "DOF/s", "cores": cores, "kind": "oracle",
+        return os.cpu_count()
+
+
+class OracleRun:
+    """The FP64 CPU oracle's complete MGCG solve (to 1e-10) of a workload sample, set up once;
+    each call of solve() is one measured solve from u_0 = 0."""
+
+    def __init__(self, w, opts):
+        from oracle.layout import to_global
+        from oracle.mg import Hierarchy as OHier
+        self.w = oracle_sample(w)
+        t0 = time.perf_counter()
+        self.h = OHier(w.dim, w.P, self.w.spacing, w.periodic, w.beta, w.mu_star, smoother=opts["smoother"],
+                       overlap=opts["overlap"], variable=opts.get("variable_v", False))
+        d = self.h.fine
+        self.F = d.rhs(to_global(syn.source_values(self.w, d.coords()), w.dim))
+        self.setup_s = time.perf_counter() - t0
+        self.ndof = d.ndof
+
+    def solve(self):
+        from oracle.mg import mgcg
+        t0 = time.perf_counter()
+        U, hist = mgcg(self.h, np.zeros_like(self.F), self.F, rtol=1e-10)
+        return time.perf_counter() - t0, len(hist) - 1
+
+    def describe(self, seconds, its):
+        return (f"{'x'.join(map(str, self.w.n_elem))} elements at P={self.w.P} ({self.ndof} DOF), full MGCG "
+                f"solve to 1e-10 ({its} iterations, {seconds:.2f} s per solve; set-up {self.setup_s:.1f} s "
+                f"excluded)")
+
+
+def oracle_baseline(w, opts, min_seconds=10.0):
+    """The FP64 CPU oracle on a bounded sample of the workload: complete solves repeated
+    until about min_seconds of CPU work; value = sample DOF x solves / their time."""
+    run = OracleRun(w, opts)
+    times, its = [], 0
+    while not times or (sum(times) < min_seconds and len(times) < 50):
+        t, its = run.solve()
+        times.append(t)
+    return {"value": run.ndof * len(times) / sum(times), "unit": "DOF/s", "cores": _cores(), "kind": "oracle",
             "threads": "NumPy: the BLAS products (tensordot, matmul) may use all the cores counted; "
                        "the element-wise work runs on one",
-            "sample": f"{'x'.join(map(str, ne))} elements at P={w.P} ({d.ndof} DOF), full MGCG solve to "
-                      f"1e-10 ({len(hist) - 1} iterations, {t2 - t1:.1f} s; set-up {t1 - t0:.1f} s excluded)",
-            "iterations": len(hist) - 1, "seconds": t2 - t1}
+            "sample": run.describe(statistics.mean(times), its) + f"; {len(times)} solves timed",
+            "iterations": its, "seconds": sum(times)}
 
 
 def batch_oracle_sample():
@@ -223,32 +261,60 @@ def batch_oracle_sample():
 
 
 def run_reference(args):
+    """The oracle as the reference arm: each step is one complete FP64 solve of the bounded
+    sample of the workload, timed on its own (no extrapolation to the full grid)."""
     rank, world = dist_init(args)
     if rank != 0:
         return
     w, opts = batch_oracle_sample() if args.workload == "c5" else workload(args.workload)
-    vals = []
-    base = None
+    run = OracleRun(w, opts)
+    times, its = [], 0
     for k in range(args.warmup + args.steps):
-        r = oracle_baseline(w, opts)
+        t, its = run.solve()
         if k >= args.warmup:
-            vals.append(r["value"])
-            base = r
-        if args.warmup + args.steps > 2 and k == 0 and r["seconds"] > 40:
-            break
-    if not vals:
-        vals = [r["value"]]
-        base = r
-    v = statistics.mean(vals)
+            times.append(t)
+    t_step = statistics.mean(times)
+    v = run.ndof / t_step
+    sample = run.describe(t_step, its)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DOF/s", "n_gpus": 0,
-            "steps": len(vals), "warmup": args.warmup, "ms_per_step": 1e3 * w.ndof / v,
+            "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": BATCH_NAME if args.workload == "c5" else w.name, "sample": base["sample"]},
-            "cpu_baseline": {"value": v, "unit": "DOF/s", "cores": base["cores"], "kind": "oracle",
-                             "sample": base["sample"]},
+            "config": {"workload": BATCH_NAME if args.workload == "c5" else w.name, "sample": sample,
+                       "ndof_per_step": run.ndof,
+                       "note": "each step solves the bounded sample; ms_per_step is its measured time"},
+            "cpu_baseline": {"value": v, "unit": "DOF/s", "cores": _cores(), "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def measure_fma_peaks(lib, stream, target_ms=20.0):
+    """FP64 and FP32 multiply-add peaks (GFLOP/s) measured now by the library's probe kernel
+    (pmg_fma_probe), timed with CUDA events on `stream`: launches sized to about target_ms,
+    the best of three."""
+    import ctypes
+    import torch
+    from paper_1603_02524_gb300 import binding
+
+    def launch(fp64, iters):
+        fl = ctypes.c_double(0.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        assert lib.pmg_fma_probe(fp64, iters, binding._stream(stream), ctypes.byref(fl)) == 0
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), fl.value
+
+    out = {}
+    for name, fp64 in (("fp64", 1), ("fp32", 0)):
+        iters = 64
+        ms, _ = launch(fp64, iters)
+        while ms < 0.5 * target_ms:
+            iters = int(iters * min(16.0, max(2.0, target_ms / max(ms, 1e-3))))
+            ms, _ = launch(fp64, iters)
+        out[name] = max(fl / (ms * 1e-3) for ms, fl in (launch(fp64, iters) for _ in range(3))) / 1e9
+    return out
 
 
 def main_batch(args):
@@ -364,11 +430,14 @@ def main_batch(args):
         ms = time_kernel(native, 10, stream, flush)
         flops = 2.0 * hb.schwarz_sweep_fma(hb.L, 0)
         fp64_main = args.precision == "fp64"
-        peak = (FP64_PEAK_GFLOPS if fp64_main else FP32_PEAK_GFLOPS) / 1e3
+        peaks = measure_fma_peaks(lib, stream)
+        peak = peaks["fp64" if fp64_main else "fp32"] / 1e3
         ach = flops / (ms * 1e-3) / 1e12
         nn = wb.P + 1 + 2 * (1 + (wb.P + 4) // 8)
         line["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                            "traffic": None,
+                            "traffic": None, "peak_source": ("FP64" if fp64_main else "FP32") + " multiply-add "
+                            "throughput measured in this run (pmg_fma_probe, CUDA events)",
+                            "measured_fma_peaks_gflops": peaks,
                             "kernel": f"fdm_kernel<{'double' if fp64_main else 'float'},{2 * wb.P},{nn},{nn}> "
                                       f"(FA patch solve, x faces, largest member {wb.name})",
                             "flops_per_launch": flops}
@@ -530,7 +599,9 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
     # passes (even-odd split on centro-symmetric axes), reported by the library
     flops = 2.0 * h.schwarz_sweep_fma(h.L, fam)
     paper_flops = 12.0 * nn ** 4 * nelem if fam == -1 else None   # the paper's n^4-per-pass count (EA)
-    peak = (FP64_PEAK_GFLOPS if fp64_main else FP32_PEAK_GFLOPS) / 1e3
+    peaks = measure_fma_peaks(lib, stream)
+    line["measured_fma_peaks_gflops"] = peaks
+    peak = peaks["fp64" if fp64_main else "fp32"] / 1e3
     # precision mixed_tf32 on 3-D patches of 13^3 nodes and more: the tcgen05 kernel, whose
     # contractions run on the tensor cores (tf32 peak)
     n_a = nn if fam == -1 else 2 * w.P
@@ -538,12 +609,12 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
     if tc5:
         peak = TF32_PEAK_GFLOPS / 1e3
     ach = flops / (ms * 1e-3) / 1e12
-    # DRAM bytes per patch of this kernel from one ncu capture of the same kernel on the
-    # 32^3-element P = 8 problem (the ncu summary of fdm_kernel<double,13> under profiles/),
-    # scaled by patches; only for the kernel version that was captured
+    # DRAM bytes per patch of this kernel version from one ncu capture (the summaries under
+    # profiles/), scaled by the patch count
     traffic = None
-    if fam == -1 and fp64_main and w.P == 8 and w.dim == 3:
-        traffic = (383.47e6 + 162.46e6) / 32768 * nelem
+    key = (tname if not tc5 else "tc", w.P, "EA" if fam == -1 else "FA", w.dim)
+    if key in TRAFFIC_PER_PATCH:
+        traffic = TRAFFIC_PER_PATCH[key] * nelem
     kname = "fdm_kernel_tc" if tc5 else f"fdm_kernel<{tname},"
     line["roofline"] = {"bound": "tensor" if tc5 else "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                         "frac": ach / peak, "traffic": traffic,
@@ -554,9 +625,9 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
                         "flops_per_launch": flops, "paper_count_flops_per_launch": paper_flops,
                         "peak_source": ("dense tf32 tensor peak = measured bf16 burst peak x 1/2; flops are "
                                         "the line passes' multiply-adds x 2 (tables unfolded)" if tc5 else
-                                        ("FP64" if fp64_main else "FP32") + " FMA throughput measured on this "
-                                        "pool's GB300 (FMA-chain probe; nominal FP64 1.25 TFLOP/s); the patch "
-                                        "solve does ~270 flop per 24 B/DOF, far above both ridges")}
+                                        ("FP64" if fp64_main else "FP32") + " multiply-add throughput measured "
+                                        "in this run (pmg_fma_probe, CUDA events); the patch solve does "
+                                        "~270-680 flop per 24 B/DOF, far above both ridges")}
     line["smoother"] = {"gdof_s": n / (ms * 1e-3) / 1e9, "ms_patch_sweep": ms,
                         "note": ("EA" if fam == -1 else "FA (one direction)")
                                 + f" patch sweep alone (gather, 6 transforms, weighted scatter), {tname}"}
@@ -598,7 +669,7 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
         ms_o = time_kernel(lambda: native(hm), 5, stream, flush)
         t_o = statistics.mean(tm)
         fl_o = 2.0 * hm.schwarz_sweep_fma(hm.L, fam)
-        pk_o = (FP64_PEAK_GFLOPS if prec == "fp64" else FP32_PEAK_GFLOPS) / 1e3
+        pk_o = peaks["fp64" if prec == "fp64" else "fp32"] / 1e3
         if prec == "mixed_tf32" and w.dim == 3 and w.P >= 8:   # tcgen05 patch kernel: tf32 tensor peak
             pk_o = TF32_PEAK_GFLOPS / 1e3
         entry = {"value": n / (t_o * 1e-3), "unit": "DOF/s", "ms_per_step": t_o, "iterations": itm,
