@@ -59,6 +59,7 @@ TF32_PEAK_GFLOPS = _tf32_peak_gflops()
 # P, family, dim).  The roofline's `traffic` scales it by the bench grid's patch count.
 TRAFFIC_PER_PATCH = {
     ("double", 8, "EA", 3): (383.47e6 + 162.46e6) / 32768,   # fdm_kernel<double,13,13,13>, 32^3 elements
+    ("double", 16, "EA", 3): (325.70e6 + 118.69e6) / 4096,   # fdm_kernel<double,23,23,23>, 16^3 elements
 }
 
 
