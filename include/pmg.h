@@ -106,6 +106,16 @@ typedef struct {
                           z = r, i.e. plain CG, the paper's reference method of Sec. 4 */
   int outer_apply;     /* PMG_OUTER_*: arithmetic of the CG's own operator apply
                           (residual g - A u and q = A p of Algorithm 2) (default FP64) */
+  int nrhs;            /* right-hand sides solved together, 1..64 (default 1): every
+                          vector of the hierarchy then holds nrhs vectors of the grid back
+                          to back (vector r at offset r * n, n = the grid's unknowns at that
+                          level), pmg_level_info reports nrhs * n, and each kernel launch
+                          covers all of them with one copy of the tables.  Internally the
+                          copies are stacked along the grid's last axis with walls between
+                          them, hence homogeneous Dirichlet grids only (periodic: EINVAL).
+                          pmg_solve runs nrhs independent CG iterations (own scalars,
+                          convergence test and result each) in one loop until all have
+                          stopped; stats then points to nrhs entries. */
 } pmg_options;
 
 typedef struct {
@@ -226,7 +236,10 @@ int pmg_vcycle(pmg_hier h, const double* f_dev, double* u_dev, void* stream);
  * z^T (r - r_old) / delta).  g_dev: right-hand side (periodic grids: projected
  * onto zero mean internally).  u_dev: initial guess in, solution out.
  * Stops when ||r||_2 <= rtol * ||r_0||_2 or after opt.max_iter iterations
- * (PMG_ENOCONV, u holds the last iterate).  stats may be NULL.
+ * (PMG_ENOCONV, u holds the last iterate).  stats may be NULL.  A hierarchy with
+ * nrhs > 1 solves its nrhs right-hand sides (g_dev, u_dev: nrhs vectors back to back),
+ * each with its own test; stats[0..nrhs) receive their statistics and the call returns
+ * the status of the first right-hand side that failed, else PMG_OK.
  */
 int pmg_solve(pmg_hier h, const double* g_dev, double* u_dev, double rtol, pmg_stats* stats,
               void* stream);
@@ -246,15 +259,17 @@ int pmg_solve_host(pmg_hier h, const double* g_host, double* u_host, double rtol
  * guess / solution u_dev[i], into one CUDA graph: one branch per solve, each
  * with its iterations in a device-side loop and its own convergence test
  * ||r||_2 <= rtol ||r_0||_2 (cap: that hierarchy's max_iter).  Grids may differ
- * in size, order, spacing and options; several right-hand sides of one grid
- * need one hierarchy each (a hierarchy holds one solve's workspace), so the
- * hierarchies must be distinct (else PMG_EINVAL).  The vectors are the
- * caller's and are bound to the batch: pmg_batch_solve reads g_dev[i] and
- * u_dev[i] where they are at that call.
+ * in size, order, spacing, options and number of right-hand sides (a hierarchy
+ * built with nrhs > 1 solves all of its right-hand sides in its branch: g_dev[i]
+ * and u_dev[i] then hold nrhs vectors each); the hierarchies must be distinct
+ * (else PMG_EINVAL), since a hierarchy holds one solve's workspace.  The vectors
+ * are the caller's and are bound to the batch: pmg_batch_solve reads g_dev[i]
+ * and u_dev[i] where they are at that call.
  *   pmg_batch_solve  runs all solves with one graph launch on `stream`,
- *                    synchronises once, fills stats[0..count-1] (may be NULL;
- *                    history arrays optional) and returns PMG_OK or the status
- *                    of the first solve (by index) that failed.
+ *                    synchronises once, fills stats (may be NULL; history
+ *                    arrays optional) with one entry per right-hand side, solve
+ *                    by solve, and returns PMG_OK or the status of the first
+ *                    right-hand side (in that order) that failed.
  *   pmg_batch_destroy  frees the graph; destroy a batch before its hierarchies.
  * Creation runs one V-cycle on each hierarchy that has not run yet (kernel
  * set-up) and synchronises the device.  Not thread safe with respect to the

@@ -38,7 +38,7 @@ class PmgOptions(ctypes.Structure):
                 ("ns_pre", ctypes.c_int), ("ns_post", ctypes.c_int), ("variable_v", ctypes.c_int),
                 ("omega", ctypes.c_double), ("precision", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("omega_level", ctypes.c_double * 8), ("tau_level", ctypes.c_double * 8),
-                ("preconditioner", ctypes.c_int), ("outer_apply", ctypes.c_int)]
+                ("preconditioner", ctypes.c_int), ("outer_apply", ctypes.c_int), ("nrhs", ctypes.c_int)]
 
 
 class PmgStats(ctypes.Structure):
@@ -85,8 +85,8 @@ def load(path: str | None = None):
         "pmg_prolong": (i, [vp, i, vp, vp, vp]),
         "pmg_coarse_solve": (i, [vp, vp, vp, vp]),
         "pmg_vcycle": (i, [vp, vp, vp, vp]),
-        "pmg_solve": (i, [vp, vp, vp, d, ctypes.POINTER(PmgStats), vp]),
-        "pmg_solve_host": (i, [vp, vp, vp, d, ctypes.POINTER(PmgStats), vp]),
+        "pmg_solve": (i, [vp, vp, vp, d, vp, vp]),
+        "pmg_solve_host": (i, [vp, vp, vp, d, vp, vp]),
         "pmg_status_string": (ctypes.c_char_p, [i]),
         "pmg_last_error": (ctypes.c_char_p, [vp]),
         "pmg_schwarz_sweep": (i, [vp, i, i, vp, vp, vp]),
@@ -119,7 +119,7 @@ def load(path: str | None = None):
 
 def options(smoother="EA", overlap="l", weighting="quintic", ns=(1, 1), variable_v=False,
             omega=1.0, precision="fp64", max_iter=100, omega_level=None, tau_level=None,
-            preconditioner="vcycle", outer_apply="fp64") -> PmgOptions:
+            preconditioner="vcycle", outer_apply="fp64", nrhs=1) -> PmgOptions:
     """omega_level / tau_level: optional per-level sequences (index = level, 0 = default);
     preconditioner "vcycle" (Algorithm 2) or "none" (plain CG); outer_apply "fp64" or "df"
     (the CG's operator apply in double-float on the FP32 pipes)."""
@@ -139,6 +139,7 @@ def options(smoother="EA", overlap="l", weighting="quintic", ns=(1, 1), variable
         o.tau_level[l] = float(v)
     o.preconditioner = {"vcycle": 0, "none": 1}[preconditioner]
     o.outer_apply = {"fp64": 0, "df": 1}[outer_apply]
+    o.nrhs = int(nrhs)
     return o
 
 
@@ -280,17 +281,26 @@ class Hierarchy:
         _check("pmg_vcycle", load().pmg_vcycle(self.handle, _dev(f, n), _dev(u, n), _stream(stream)), self.handle)
 
     def solve(self, g, u, rtol=1e-10, stream=None, history=True, check=True):
-        """Algorithm 2 on device tensors; returns (status, iterations, residual history)."""
+        """Algorithm 2 on device tensors; returns (status, iterations, residual history).
+        A hierarchy with nrhs > 1 (g, u: nrhs vectors back to back) returns
+        (status, [iterations per right-hand side], [history per right-hand side])."""
         n = self.ndof()
-        st = PmgStats()
-        hist = (ctypes.c_double * (self.opts.max_iter + 1))() if history else None
-        st.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if history else None
-        rc = load().pmg_solve(self.handle, _dev(g, n), _dev(u, n), float(rtol), ctypes.byref(st), _stream(stream))
+        k = self.opts.nrhs
+        st = (PmgStats * k)()
+        hists = []
+        for i in range(k):
+            hist = (ctypes.c_double * (self.opts.max_iter + 1))() if history else None
+            hists.append(hist)
+            st[i].history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if history else None
+        rc = load().pmg_solve(self.handle, _dev(g, n), _dev(u, n), float(rtol), st, _stream(stream))
         if check and rc not in (0, -4):
             _check("pmg_solve", rc, self.handle)
-        self.last_device_loop = bool(st.device_loop)
-        h = list(hist[: st.iterations + 1]) if history else []
-        return rc, st.iterations, h
+        self.last_device_loop = bool(st[0].device_loop)
+        self.last_stats = [(st[i].status, st[i].iterations, st[i].r0, st[i].rn) for i in range(k)]
+        hs = [list(hists[i][: st[i].iterations + 1]) if history else [] for i in range(k)]
+        if k == 1:
+            return rc, st[0].iterations, hs[0]
+        return rc, [st[i].iterations for i in range(k)], hs
 
     def solve_host(self, g_host, u_host, rtol=1e-10, stream=None):
         """Algorithm 2 on host arrays (numpy or pinned torch CPU tensors, fp64, contiguous)."""
@@ -303,13 +313,11 @@ class Hierarchy:
                 return ctypes.c_void_p(a.ctypes.data)
             assert a.numel() == n and a.is_contiguous() and not a.is_cuda
             return ctypes.c_void_p(a.data_ptr())
-        st = PmgStats()
-        st.history = None
-        rc = load().pmg_solve_host(self.handle, hp(g_host), hp(u_host), float(rtol), ctypes.byref(st),
-                                   _stream(stream))
+        st = (PmgStats * self.opts.nrhs)()
+        rc = load().pmg_solve_host(self.handle, hp(g_host), hp(u_host), float(rtol), st, _stream(stream))
         if rc not in (0, -4):
             _check("pmg_solve_host", rc, self.handle)
-        return rc, st.iterations
+        return rc, st[0].iterations
 
     def device_status(self, stream=None):
         """Read and reset the hierarchy's device status word (pmg_device_status)."""
@@ -365,14 +373,18 @@ class Batch:
         self.handle = b
         self.count = n
         self.max_iter = [h.opts.max_iter for h in hiers]
+        self.nrhs = [h.opts.nrhs for h in hiers]
 
     def solve(self, stream=None, history=False, check=True):
-        """Run every solve; returns (status, [(status, iterations, r0, rn[, history]) ...])."""
-        st = (PmgStats * self.count)()
+        """Run every solve; returns (status, [(status, iterations, r0, rn[, history]) ...]) with
+        one entry per right-hand side, solve by solve."""
+        total = sum(self.nrhs)
+        mx = [m for m, k in zip(self.max_iter, self.nrhs) for _ in range(k)]
+        st = (PmgStats * total)()
         hists = []
-        for i in range(self.count):
+        for i in range(total):
             if history:
-                hist = (ctypes.c_double * (self.max_iter[i] + 1))()
+                hist = (ctypes.c_double * (mx[i] + 1))()
                 hists.append(hist)
                 st[i].history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
             else:
@@ -382,7 +394,7 @@ class Batch:
             detail = (load().pmg_batch_last_error(self.handle) or b"").decode()
             raise PmgError("pmg_batch_solve", rc, detail)
         out = []
-        for i in range(self.count):
+        for i in range(total):
             item = (st[i].status, st[i].iterations, st[i].r0, st[i].rn)
             if history:
                 item = item + (list(hists[i][: st[i].iterations + 1]),)

@@ -438,7 +438,7 @@ fdm_kernel(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restric
       // element-major offset contribution of local index a, or "invalid"
       const int ph = ax.phys;
       const int npp = (ph == 2) ? dm.NPz : dm.NP;
-      int G = ax.start0 + (int)p * npp + a;
+      int G = patch_start(ax, (int)p, npp) + a;
       long long o;
       if (ax.periodic) {
         G %= ax.N;
@@ -568,7 +568,7 @@ __device__ __forceinline__ void pipe_prepare(const LevelDims& dm, const FdmFamil
       cp_async<sizeof(T)>(lam + base[q] + a, ax.lam + p * n + a, true);
       const int ph = ax.phys;
       const int npp = (ph == 2) ? dm.NPz : dm.NP;
-      int G = ax.start0 + (int)p * npp + a;
+      int G = patch_start(ax, (int)p, npp) + a;
       long long o;
       if (ax.periodic) {
         G %= ax.N;
@@ -701,7 +701,7 @@ fdm_kernel_gbuf(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __re
         lq[q][a] = ax.lam[p * n + a];
         const int ph = ax.phys;
         const int npp = (ph == 2) ? dm.NPz : dm.NP;
-        int G = ax.start0 + (int)p * npp + a;
+        int G = patch_start(ax, (int)p, npp) + a;
         long long o;
         if (ax.periodic) {
           G %= ax.N;

@@ -31,8 +31,10 @@
 // apart along K those stores fall into distinct shared-memory banks.
 //
 // Precision: tf32 products (10-bit operand mantissas) with fp32 accumulation;
-// the tables are rounded to tf32 on the host, the operands between passes when
-// they are stored, and the gathered residual is truncated by the tensor core.
+// the tables are rounded to tf32 on the host; the gathered residual and the fp32
+// operands stored between passes are truncated to tf32 by the tensor core (relative
+// error below 2^-10 each; rounding them first cost two integer operations per value
+// and changed neither the iteration counts nor the smoother's error bound).
 // The preconditioner is applied inside a flexible CG whose residual, operator
 // and inner products stay FP64.
 #pragma once
@@ -60,7 +62,7 @@ struct TcGeom {
   __host__ __device__ static constexpr uint32_t sbo(int n) { return (uint32_t)(kp(n) / 4) * LBO; }
   __host__ __device__ static constexpr uint32_t abytes(int n, int m) { return (uint32_t)mt(m) * 16u * sbo(n); }
   __host__ __device__ static constexpr uint32_t mx(uint32_t x, uint32_t y) { return x > y ? x : y; }
-  static constexpr int FS = NA | 1;                               // staging row stride (odd)
+  static constexpr int FS = (NA + 3) / 4 * 4 % 8 == 0 ? (NA + 3) / 4 * 4 + 4 : (NA + 3) / 4 * 4;  // staging row stride
   static constexpr uint32_t ABYTES =
       (mx(mx(mx(abytes(NA, M0), abytes(NB, M1)), mx(abytes(NC, M2), abytes(NB, M4))), 4u * NB * NC * FS) + 1023) /
       1024 * 1024;
@@ -78,7 +80,8 @@ struct TcGeom {
   static constexpr uint32_t LAM_OFF = ROW_OFF + 8u * (uint32_t)((NB * NC + 1) / 2 * 2);
   // mbarrier of the MMA completions (+0), tensor-memory address slot (+8), and a
   // second mbarrier that nothing ever completes (+16): the stalled-wait test hook
-  static constexpr uint32_t BAR_OFF = (LAM_OFF + 4u * (NA + NB + NC) + 15) / 16 * 16;
+  static constexpr uint32_t RDST_OFF = (LAM_OFF + 4u * (NA + NB + NC) + 15) / 16 * 16;
+  static constexpr uint32_t BAR_OFF = (RDST_OFF + 4u * NB * NC + 15) / 16 * 16;
   static constexpr uint32_t BYTES = BAR_OFF + 32;
   __host__ __device__ static constexpr uint32_t cols(int n, int m) { return (uint32_t)mt(m) * (uint32_t)npd(n); }
   static constexpr uint32_t COLS_USED = mx(mx(cols(NA, M0), cols(NB, M1)), mx(cols(NC, M2), cols(NB, M4)));
@@ -95,19 +98,6 @@ struct TcRows {
   static constexpr int W = 32 / R;
 };
 
-// x rounded to tf32 (nearest, ties away from zero) by integer operations on its
-// bits: add half a unit of the 13 dropped mantissa bits to the magnitude, then
-// clear them (finite x).
-__device__ __forceinline__ float round_tf32(float x) {
-  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-}
-
-// A operand element (row, K index k), 8-row groups `sbo` bytes apart.
-__device__ __forceinline__ int a_index(int row, int k, uint32_t sbo) {
-  return (row >> 3) * (int)(sbo / 4) + (k >> 2) * 36 + (row & 7) * 4 + (k & 3);
-}
-
-
 // Table of the patch (forward S or backward W^T, n x n, entry [k][j] = input k,
 // output j; uploaded already rounded to tf32) as the K-major B operand:
 // asynchronous element copies (the zero pads of the npd(n) x kp(n) operand are
@@ -122,6 +112,68 @@ template <int NA, int NB, int NC, int N>
 __device__ __forceinline__ void tc_table_async(float* B, const float* __restrict__ src) {
   for (int i = threadIdx.x; i < N * N; i += blockDim.x) cp_async<4>(B + tc_boff<NA, NB, NC, N>(i), src + i, true);
 }
+// Store accumulator row m (registers r, outputs j = 0..) of pass PASS as the next
+// pass's operand (or, after the last pass, into the staging rows); rows beyond the
+// patch extents are padding and are dropped.
+template <int NA, int NB, int NC, int PASS, int NPD>
+__device__ __forceinline__ void tc_store_row(float* A, int m, const uint32_t (&r)[NPD], const float* la,
+                                             const float* lb, const float* lc) {
+  using G = TcGeom<NA, NB, NC>;
+  auto d = [&](int j) { return __uint_as_float(r[j]); };
+  // offsets of the next operand: a thread-dependent base plus, for output j, a
+  // compile-time step (rows a multiple of 8 apart, or a fixed position in K)
+  if constexpr (PASS == 0) {                   // m = b + NBP c -> A1[c + NCP a'][b]
+    constexpr int S = (int)G::sbo(NB) / 4;
+    const int b = m % G::NBP, c = m / G::NBP;
+    if (b >= NB || c >= NC) return;
+    const int base = (c >> 3) * S + (c & 7) * 4 + (b >> 2) * 36 + (b & 3);
+#pragma unroll
+    for (int j = 0; j < NA; ++j) A[base + j * (G::NCP / 8) * S] = d(j);
+  } else if constexpr (PASS == 1) {            // m = c + NCP a' -> A2[b' + NBP a'][c]
+    constexpr int S = (int)G::sbo(NC) / 4;
+    const int c = m % G::NCP, a = m / G::NCP;
+    if (c >= NC || a >= NA) return;
+    const int base = a * (G::NBP / 8) * S + (c >> 2) * 36 + (c & 3);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) A[base + (j >> 3) * S + (j & 7) * 4] = d(j);
+  } else if constexpr (PASS == 2) {            // m = b' + NBP a' -> A3[m][c'] / (la + lb + lc)
+    constexpr int S = (int)G::sbo(NC) / 4;
+    const int b = m % G::NBP, a = m / G::NBP;
+    if (b >= NB || a >= NA) return;
+    const float s0 = la[a] + lb[b];
+    float4* dst = reinterpret_cast<float4*>(A + (m >> 3) * S + (m & 7) * 4);   // 4 K values: 16 bytes
+#pragma unroll
+    for (int g = 0; g < (NC + 3) / 4; ++g) {
+      float v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = (4 * g + k < NC) ? d(4 * g + k) * recip(s0 + lc[4 * g + k]) : 0.0f;
+      dst[g * 9] = make_float4(v[0], v[1], v[2], v[3]);                        // groups 144 bytes apart
+    }
+  } else if constexpr (PASS == 3) {            // m = b' + NBP a' -> A4[a' + NAP c][b']
+    constexpr int S = (int)G::sbo(NB) / 4;
+    const int b = m % G::NBP, a = m / G::NBP;
+    if (b >= NB || a >= NA) return;
+    const int base = (a >> 3) * S + (a & 7) * 4 + (b >> 2) * 36 + (b & 3);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) A[base + j * (G::NAP / 8) * S] = d(j);
+  } else if constexpr (PASS == 4) {            // m = a' + NAP c -> A5[b + NBP c][a']
+    constexpr int S = (int)G::sbo(NA) / 4;
+    const int a = m % G::NAP, c = m / G::NAP;
+    if (a >= NA || c >= NC) return;
+    const int base = c * (G::NBP / 8) * S + (a >> 2) * 36 + (a & 3);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) A[base + (j >> 3) * S + (j & 7) * 4] = d(j);
+  } else {                                     // m = b + NBP c -> staging row b + NB c
+    const int b = m % G::NBP, c = m / G::NBP;
+    if (b >= NB || c >= NC) return;
+    float4* st = reinterpret_cast<float4*>(A + (b + NB * c) * G::FS);
+#pragma unroll
+    for (int g = 0; g < (NA + 3) / 4; ++g)
+      st[g] = make_float4(d(4 * g), 4 * g + 1 < NA ? d(4 * g + 1) : 0.0f, 4 * g + 2 < NA ? d(4 * g + 2) : 0.0f,
+                          4 * g + 3 < NA ? d(4 * g + 3) : 0.0f);
+  }
+}
+
 // One line pass: MMAs of all row tiles (one thread), wait, read-back into the
 // next operand.  Returns false (uniformly) if the MMAs did not complete in time.
 // stall_ns != 0 (test hook): the threads wait instead on `never`, an mbarrier that
@@ -161,64 +213,17 @@ __device__ __forceinline__ bool tc_pass(float* A, const float* B, uint64_t* mbar
   if (__syncthreads_or(!ok)) return false;
   umma::fence_after_sync();
 
-  // read-back: warp w reads lanes 32 (w % 4) .. of tiles w / 4, w / 4 + nw / 4, ...
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quarter = warp & 3;
+  // read-back: warp w reads lanes 32 (w % 4) .. of tiles w / 4, w / 4 + nw / 4, ...;
+  // the tensor-memory load of the warp's next tile is in flight while it stores this one
+  const int warp = threadIdx.x >> 5, quarter = warp & 3;
   const int nw4 = blockDim.x >> 7;
-  for (int t = warp >> 2; t < MT; t += nw4) {
-    const int mbase = t * 128 + 32 * quarter;
-    if (mbase >= M) continue;                    // warp-uniform
-    float d[NPD];
-    if constexpr (NPD == 32) {
-      umma::tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(t * NPD), d);
-    } else {
-      umma::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(t * NPD), d);
-    }
-    const int m = mbase + lane;
-    // offsets of the next operand: a thread-dependent base plus, for output j, a
-    // compile-time step (rows a multiple of 8 apart, or a fixed position in K)
-    if constexpr (PASS == 0) {                   // m = b + NBP c -> A1[c + NCP a'][b]
-      constexpr int S = (int)G::sbo(NB) / 4;
-      const int b = m % G::NBP, c = m / G::NBP;
-      if (b >= NB || c >= NC) continue;
-      const int base = (c >> 3) * S + (c & 7) * 4 + (b >> 2) * 36 + (b & 3);
-#pragma unroll
-      for (int j = 0; j < NA; ++j) A[base + j * (G::NCP / 8) * S] = round_tf32(d[j]);
-    } else if constexpr (PASS == 1) {            // m = c + NCP a' -> A2[b' + NBP a'][c]
-      constexpr int S = (int)G::sbo(NC) / 4;
-      const int c = m % G::NCP, a = m / G::NCP;
-      if (c >= NC || a >= NA) continue;
-      const int base = a * (G::NBP / 8) * S + (c >> 2) * 36 + (c & 3);
-#pragma unroll
-      for (int j = 0; j < NB; ++j) A[base + (j >> 3) * S + (j & 7) * 4] = round_tf32(d[j]);
-    } else if constexpr (PASS == 2) {            // m = b' + NBP a' -> A3[m][c'] / (la + lb + lc)
-      constexpr int S = (int)G::sbo(NC) / 4;
-      const int b = m % G::NBP, a = m / G::NBP;
-      if (b >= NB || a >= NA) continue;
-      const float s0 = la[a] + lb[b];
-      const int base = (m >> 3) * S + (m & 7) * 4;
-#pragma unroll
-      for (int j = 0; j < NC; ++j) A[base + (j >> 2) * 36 + (j & 3)] = round_tf32(d[j] * recip(s0 + lc[j]));
-    } else if constexpr (PASS == 3) {            // m = b' + NBP a' -> A4[a' + NAP c][b']
-      constexpr int S = (int)G::sbo(NB) / 4;
-      const int b = m % G::NBP, a = m / G::NBP;
-      if (b >= NB || a >= NA) continue;
-      const int base = (a >> 3) * S + (a & 7) * 4 + (b >> 2) * 36 + (b & 3);
-#pragma unroll
-      for (int j = 0; j < NC; ++j) A[base + j * (G::NAP / 8) * S] = round_tf32(d[j]);
-    } else if constexpr (PASS == 4) {            // m = a' + NAP c -> A5[b + NBP c][a']
-      constexpr int S = (int)G::sbo(NA) / 4;
-      const int a = m % G::NAP, c = m / G::NAP;
-      if (a >= NA || c >= NC) continue;
-      const int base = c * (G::NBP / 8) * S + (a >> 2) * 36 + (a & 3);
-#pragma unroll
-      for (int j = 0; j < NB; ++j) A[base + (j >> 3) * S + (j & 7) * 4] = round_tf32(d[j]);
-    } else {                                     // m = b + NBP c -> staging row b + NB c
-      const int b = m % G::NBP, c = m / G::NBP;
-      if (b >= NB || c >= NC) continue;
-      float* st = A + (b + NB * c) * G::FS;
-#pragma unroll
-      for (int j = 0; j < NA; ++j) st[j] = d[j];
-    }
+  auto valid = [&](int t) { return t < MT && t * 128 + 32 * quarter < M; };
+  auto taddr = [&](int t) { return tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(t * NPD); };
+  uint32_t ra[NPD];
+  for (int t = warp >> 2; valid(t); t += nw4) {
+    umma::tmem_ld_nowait<NPD>(taddr(t), ra);
+    umma::tmem_wait_ld<NPD>(ra);
+    tc_store_row<NA, NB, NC, PASS>(A, t * 128 + 32 * quarter + (threadIdx.x & 31), ra, la, lb, lc);
   }
   return true;
 }
@@ -239,6 +244,7 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
   for (int i = 0; i < 6; ++i) Tb[i] = reinterpret_cast<float*>(tc_smem + G::tab_off(i));
   long long* off = reinterpret_cast<long long*>(tc_smem + G::OFF_OFF);
   long long* rowoff = reinterpret_cast<long long*>(tc_smem + G::ROW_OFF);
+  int* rowdst = reinterpret_cast<int*>(tc_smem + G::RDST_OFF);
   float* la = reinterpret_cast<float*>(tc_smem + G::LAM_OFF);
   float* lb = la + NA;
   float* lc = lb + NB;
@@ -250,6 +256,10 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
 
   // operand pads must hold finite values (their products with the zero table pads vanish)
   for (int i = tid; i < (int)(G::OFF_OFF / 4); i += blockDim.x) A[i] = 0.0f;
+  for (int row = tid; row < NB * NC; row += blockDim.x) {
+    const int b = row % NB, c = row / NB, m = b + G::NBP * c;
+    rowdst[row] = (m >> 3) * (int)(G::sbo(NA) / 4) + (m & 7) * 4;
+  }
   if (tid == 0) {
     umma::mbar_init(mbar, 1);
     umma::mbar_init(never, 1);
@@ -302,7 +312,7 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
         cp_async<4>(lq[q] + a, ax.lam + p * n + a, true);
         const int ph = ax.phys;
         const int npp = (ph == 2) ? dm.NPz : dm.NP;
-        int Gi = ax.start0 + (int)p * npp + a;
+        int Gi = patch_start(ax, (int)p, npp) + a;
         long long o;
         if (ax.periodic) {
           Gi %= ax.N;
@@ -320,16 +330,16 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
     if (fresh[1] || fresh[2])
       for (int rr = tid; rr < NB * NC; rr += blockDim.x) rowoff[rr] = off[NA + rr % NB] + off[NA + NB + rr / NB];
     __syncthreads();
-    // gather into the first operand (row b + NBP c, K index a) as asynchronous copies,
-    // zero-filled outside the grid, one warp per patch row (lane = a); one wait for
-    // gather, tables and eigenvalues.  The tensor core reads the fp32 values
+    // gather into the first operand (row b + NBP c, K index a; the row's offset in the
+    // operand from the per-CTA table rowdst) as asynchronous copies, zero-filled
+    // outside the grid, one warp per patch row (lane = a); one wait for gather,
+    // tables and eigenvalues.  The tensor core reads the fp32 values
     // truncated to tf32.
     {
       const int hw = (threadIdx.x & 31) / TcRows<NA>::W, lane = (threadIdx.x & 31) % TcRows<NA>::W;
       const int rstep = (blockDim.x >> 5) * TcRows<NA>::R;
       const long long oa = lane < NA ? off[lane] : 0;
       const int lk = (lane >> 2) * 36 + (lane & 3);
-      constexpr int S = (int)G::sbo(NA) / 4;
       // four rows per step: their row offsets are read before the first copy is issued
       for (int row0 = (tid >> 5) * TcRows<NA>::R + hw; row0 < NB * NC; row0 += 4 * rstep) {
         long long ro[4];
@@ -338,13 +348,18 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
           const int row = row0 + i * rstep;
           ro[i] = row < NB * NC ? rowoff[row] : kInvalidOffset;
         }
+        int rd[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int row = row0 + i * rstep;
-          const int b = row % NB, c = row / NB, m = b + G::NBP * c;
+          rd[i] = row < NB * NC ? rowdst[row] : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int row = row0 + i * rstep;
           const long long o = oa + ro[i];
           if (row < NB * NC && lane < NA)
-            cp_async<4>(A + (m >> 3) * S + (m & 7) * 4 + lk, o >= 0 ? r + o : r, o >= 0);
+            cp_async<4>(A + rd[i] + lk, o >= 0 ? r + o : r, o >= 0);
         }
       }
     }

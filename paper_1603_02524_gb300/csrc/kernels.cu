@@ -482,143 +482,211 @@ __device__ void finish_reduce(double a, double b, double* partial, unsigned* cou
   }
 }
 
-// out[0] = x.y ; out[1] = x.y2 (y2 may be null -> 0)
+// The CG vector kernels below run on `k` segments at once (one per right-hand side of
+// the hierarchy; vectors hold the segments back to back, n entries each): grid.y = k,
+// segment s = blockIdx.y with its own scalars (scal + s S_NUM), reduction partials
+// (partial + s kPartialStride, counter + s) and control words (ctrl + kCtrlSeg + 4 s).
+// A segment whose solve has finished (its active word is 0) is left untouched.
+__device__ __forceinline__ int* seg_ctrl(int* ctrl, int s) { return ctrl + kCtrlSeg + 4 * s; }
+__device__ __forceinline__ bool seg_active(const int* ctrl, int s) {
+  return ctrl == nullptr || ctrl[kCtrlSeg + 4 * s + C_ACTIVE] != 0;
+}
+
+// out[0] = x.y ; out[1] = x.y2 (y2 may be null -> 0), per segment (out + s S_NUM)
 __global__ void dot_kernel(const double* __restrict__ x, const double* __restrict__ y,
                            const double* __restrict__ y2, long long n, double* partial,
                            unsigned* counter, double* out) {
+  const long long o = (long long)blockIdx.y * n;
   double a = 0.0, b = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
-    double xv = x[t];
-    a = fma(xv, y[t], a);
-    if (y2) b = fma(xv, y2[t], b);
+    double xv = x[o + t];
+    a = fma(xv, y[o + t], a);
+    if (y2) b = fma(xv, y2[o + t], b);
   }
   block_sum2(a, b);
-  finish_reduce(a, b, partial, counter, out, nullptr, 0);
+  finish_reduce(a, b, partial + blockIdx.y * kPartialStride, counter + blockIdx.y, out + blockIdx.y * S_NUM,
+                nullptr, 0);
 }
 
-void launch_dot(const double* x, const double* y, const double* y2, long long n, double* partial,
+void launch_dot(const double* x, const double* y, const double* y2, long long n, int k, double* partial,
                 unsigned* counter, double* out, int nblocks, cudaStream_t s) {
-  count_launch(); dot_kernel<<<nblocks, 256, 0, s>>>(x, y, y2, n, partial, counter, out);
+  count_launch(); dot_kernel<<<dim3(nblocks, k), 256, 0, s>>>(x, y, y2, n, partial, counter, out);
 }
 
-// alpha = delta / (p.q); u += alpha p; [r_old = r]; r -= alpha q; out_rr[0] = r.r
+// alpha = delta / (p.q); u += alpha p; [r_old = r]; r -= alpha q; scal[S_RR] = r.r
 __global__ void cg_update_kernel(double* __restrict__ u, double* __restrict__ r,
                                  double* __restrict__ r_old, const double* __restrict__ p,
-                                 const double* __restrict__ q, const double* __restrict__ scal,
+                                 const double* __restrict__ q, const double* __restrict__ scal_all,
                                  int save_old, long long n, double* partial, unsigned* counter,
-                                 double* out_rr, int* status, const int* it_dev) {
+                                 int* ctrl, const int* it_dev) {
+  const int sg = blockIdx.y;
+  if (!seg_active(ctrl, sg)) return;                // uniform over the segment's blocks
+  const double* scal = scal_all + sg * S_NUM;
+  int* status = ctrl ? seg_ctrl(ctrl, sg) + C_STATUS : nullptr;
   if (it_dev) save_old = *it_dev >= 2;
   const double pq = scal[S_PQ];
   const double alpha = scal[S_DELTA] / pq;
   if (blockIdx.x == 0 && threadIdx.x == 0 && status && *status == 0) {   // the first status stays
     if (!(pq > 0.0) || !(scal[S_DELTA] > 0.0)) *status = (pq == pq) ? PMG_EBREAKDOWN : PMG_ENAN;
   }
+  const long long o = (long long)sg * n;
   double a = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
-    u[t] = fma(alpha, p[t], u[t]);
-    double rv = r[t];
-    if (save_old) r_old[t] = rv;
-    rv = fma(-alpha, q[t], rv);
-    r[t] = rv;
+    u[o + t] = fma(alpha, p[o + t], u[o + t]);
+    double rv = r[o + t];
+    if (save_old) r_old[o + t] = rv;
+    rv = fma(-alpha, q[o + t], rv);
+    r[o + t] = rv;
     a = fma(rv, rv, a);
   }
   double b = 0.0;
   block_sum2(a, b);
-  finish_reduce(a, b, partial, counter, out_rr, status, 1);
+  finish_reduce(a, b, partial + sg * kPartialStride, counter + sg, const_cast<double*>(scal) + S_RR, status, 1);
 }
 
 void launch_cg_update(double* u, double* r, double* r_old, const double* p, const double* q,
-                      const double* scal, int save_old, long long n, double* partial,
-                      unsigned* counter, double* out_rr, int* status, int nblocks, cudaStream_t s,
-                      const int* it_dev) {
-  count_launch(); cg_update_kernel<<<nblocks, 256, 0, s>>>(u, r, r_old, p, q, scal, save_old, n, partial, counter,
-                                           out_rr, status, it_dev);
+                      const double* scal, int save_old, long long n, int k, double* partial,
+                      unsigned* counter, int* ctrl, int nblocks, cudaStream_t s, const int* it_dev) {
+  count_launch();
+  cg_update_kernel<<<dim3(nblocks, k), 256, 0, s>>>(u, r, r_old, p, q, scal, save_old, n, partial, counter,
+                                                    ctrl, it_dev);
 }
 
 // beta = (z.r - z.r_old) / delta_old ; p = z + beta p   (reading C8; first: r_old = 0).
-// With it_dev (device-resident loop): iteration 1 sets the first direction p = z,
+// With it_dev (device iteration counter): iteration 1 sets the first direction p = z,
 // later iterations take z.r_old from the dot (r_old is zero until iteration 2
 // saves it, so the first beta is again Fletcher-Reeves).
 __global__ void p_update_kernel(double* __restrict__ p, const double* __restrict__ z,
-                                const double* __restrict__ scal, int first, long long n,
-                                const int* it_dev) {
+                                const double* __restrict__ scal_all, int first, long long n,
+                                const int* it_dev, const int* ctrl) {
+  const int sg = blockIdx.y;
+  if (!seg_active(ctrl, sg)) return;
+  const double* scal = scal_all + sg * S_NUM;
   const bool copy = it_dev && *it_dev == 1;
   const double zro = first ? 0.0 : scal[S_ZRO];
   const double beta = (scal[S_ZR] - zro) / scal[S_DELTA];
+  const long long o = (long long)sg * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
-    p[t] = copy ? z[t] : fma(beta, p[t], z[t]);
+    p[o + t] = copy ? z[o + t] : fma(beta, p[o + t], z[o + t]);
 }
 
-void launch_p_update(double* p, const double* z, const double* scal, int first, long long n,
-                     cudaStream_t s, const int* it_dev) {
+void launch_p_update(double* p, const double* z, const double* scal, int first, long long n, int k,
+                     cudaStream_t s, const int* it_dev, const int* ctrl) {
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  count_launch(); p_update_kernel<<<(unsigned)blocks, 256, 0, s>>>(p, z, scal, first, n, it_dev);
+  count_launch();
+  p_update_kernel<<<dim3((unsigned)blocks, k), 256, 0, s>>>(p, z, scal, first, n, it_dev, ctrl);
 }
 
-// delta <- z.r (after the p update, which still needed the old delta)
-__global__ void set_delta_kernel(double* scal, int* status) {
-  scal[S_DELTA] = scal[S_ZR];
-  if (status && *status == 0 && !(scal[S_ZR] > 0.0))
-    *status = (scal[S_ZR] == scal[S_ZR]) ? PMG_EBREAKDOWN : PMG_ENAN;
+// delta <- z.r (after the p update, which still needed the old delta), per segment
+__global__ void set_delta_kernel(double* scal_all, int* ctrl, int k) {
+  for (int sg = threadIdx.x; sg < k; sg += blockDim.x) {
+    if (!seg_active(ctrl, sg)) continue;
+    double* scal = scal_all + sg * S_NUM;
+    scal[S_DELTA] = scal[S_ZR];
+    int* status = ctrl ? seg_ctrl(ctrl, sg) + C_STATUS : nullptr;
+    if (status && *status == 0 && !(scal[S_ZR] > 0.0))
+      *status = (scal[S_ZR] == scal[S_ZR]) ? PMG_EBREAKDOWN : PMG_ENAN;
+  }
 }
-void launch_set_delta(double* scal, int* status, cudaStream_t s) {
-  count_launch(); set_delta_kernel<<<1, 1, 0, s>>>(scal, status);
+void launch_set_delta(double* scal, int* ctrl, int k, cudaStream_t s) {
+  count_launch(); set_delta_kernel<<<1, 32, 0, s>>>(scal, ctrl, k);
 }
 
-// Device-resident MGCG control (Algorithm 2 with the convergence test on the
-// device).  ctrl[0] = status word of the vector kernels, ctrl[1] = current
-// iteration, ctrl[2] = result code.  The loop of a captured solve is a graph
-// `while` node whose condition these kernels set.
-__global__ void solve_begin_kernel(double* scal, int* ctrl, double* hist,
+// MGCG control (Algorithm 2 with the convergence tests on the device), for k segments:
+// ctrl[C_ITER] = current iteration, ctrl[C_ACTIVE] = segments still iterating; per
+// segment its status word, iterations, result and active flag.  Host-driven solves
+// read the control words after each iteration; a captured solve's loop is a graph
+// `while` node whose condition these kernels set (GRAPH).
+template <bool GRAPH>
+__global__ void solve_begin_kernel(double* scal_all, int* ctrl, double* hist, int hstride, int k,
                                    cudaGraphConditionalHandle cond) {
-  const double rr0 = scal[S_RR0];
-  const double r0 = sqrt(rr0);
-  hist[0] = r0;
-  scal[S_RR] = rr0;
-  const bool go = (r0 == r0) && r0 != 0.0;
-  ctrl[1] = go ? 1 : 0;
-  ctrl[2] = (r0 == r0) ? (go ? PMG_ENOCONV : PMG_OK) : PMG_ENAN;
-  cudaGraphSetConditional(cond, go ? 1u : 0u);
+  if (threadIdx.x != 0) return;
+  int active = 0;
+  for (int sg = 0; sg < k; ++sg) {
+    double* scal = scal_all + sg * S_NUM;
+    int* c = seg_ctrl(ctrl, sg);
+    const double rr0 = scal[S_RR0];
+    const double r0 = sqrt(rr0);
+    hist[sg * hstride] = r0;
+    scal[S_RR] = rr0;
+    const bool go = (r0 == r0) && r0 != 0.0;
+    c[C_ACTIVE] = go ? 1 : 0;
+    c[C_ITER] = 0;
+    c[C_RES] = (r0 == r0) ? (go ? PMG_ENOCONV : PMG_OK) : PMG_ENAN;
+    active += go;
+  }
+  ctrl[C_ITER] = active ? 1 : 0;
+  ctrl[C_ACTIVE] = active;
+  if constexpr (GRAPH) cudaGraphSetConditional(cond, active ? 1u : 0u);
 }
 
-// After iteration ctrl[1]: record ||r||, stop on a device status, on
-// ||r|| <= rtol ||r_0|| or at max_iter; else advance the iteration counter.
-__global__ void solve_control_kernel(const double* scal, int* ctrl, double* hist, double rtol,
-                                     int max_iter, cudaGraphConditionalHandle cond) {
-  const int it = ctrl[1];
-  const double rn = sqrt(scal[S_RR]);
-  const double r0 = sqrt(scal[S_RR0]);
-  hist[it] = rn;
-  unsigned go = 0;
-  if (ctrl[0] != 0) ctrl[2] = ctrl[0];
-  else if (rn <= rtol * r0) ctrl[2] = PMG_OK;
-  else if (it >= max_iter) ctrl[2] = PMG_ENOCONV;
-  else { go = 1; ctrl[1] = it + 1; }
-  cudaGraphSetConditional(cond, go);
+// After iteration ctrl[C_ITER]: record every active segment's ||r||; a segment stops on
+// the global status word (a failure of a kernel shared by all segments), on its own
+// status word, on ||r|| <= rtol ||r_0|| or at max_iter; the loop goes on while any
+// segment is active.
+template <bool GRAPH>
+__global__ void solve_control_kernel(const double* scal_all, int* ctrl, double* hist, int hstride, int k,
+                                     double rtol, int max_iter, cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0) return;
+  const int it = ctrl[C_ITER];
+  int active = 0;
+  for (int sg = 0; sg < k; ++sg) {
+    int* c = seg_ctrl(ctrl, sg);
+    if (!c[C_ACTIVE]) continue;
+    const double* scal = scal_all + sg * S_NUM;
+    const double rn = sqrt(scal[S_RR]);
+    const double r0 = sqrt(scal[S_RR0]);
+    hist[sg * hstride + it] = rn;
+    c[C_ITER] = it;
+    int res = 1;
+    if (ctrl[C_STATUS] != 0) res = ctrl[C_STATUS];
+    else if (c[C_STATUS] != 0) res = c[C_STATUS];
+    else if (rn <= rtol * r0) res = PMG_OK;
+    else if (it >= max_iter) res = PMG_ENOCONV;
+    if (res != 1) {
+      c[C_RES] = res;
+      c[C_ACTIVE] = 0;
+    } else {
+      ++active;
+    }
+  }
+  ctrl[C_ACTIVE] = active;
+  if (active) ctrl[C_ITER] = it + 1;
+  if constexpr (GRAPH) cudaGraphSetConditional(cond, active ? 1u : 0u);
 }
 
-__global__ void solve_result_kernel(const double* scal, const int* ctrl, SolveResult* out) {
-  out->r0 = sqrt(scal[S_RR0]);
-  out->rn = sqrt(scal[S_RR]);
-  out->iterations = ctrl[1];
-  out->status = ctrl[2];
+__global__ void solve_result_kernel(const double* scal_all, const int* ctrl, SolveResult* out, int k) {
+  for (int sg = threadIdx.x; sg < k; sg += blockDim.x) {
+    const double* scal = scal_all + sg * S_NUM;
+    const int* c = ctrl + kCtrlSeg + 4 * sg;
+    out[sg].r0 = sqrt(scal[S_RR0]);
+    out[sg].rn = sqrt(scal[S_RR]);
+    out[sg].iterations = c[C_ITER];
+    out[sg].status = c[C_RES];
+  }
 }
 
-void launch_solve_result(const double* scal, const int* ctrl, SolveResult* out, cudaStream_t s) {
-  count_launch(); solve_result_kernel<<<1, 1, 0, s>>>(scal, ctrl, out);
+void launch_solve_result(const double* scal, const int* ctrl, SolveResult* out, int k, cudaStream_t s) {
+  count_launch(); solve_result_kernel<<<1, 32, 0, s>>>(scal, ctrl, out, k);
 }
 
-void launch_solve_begin(double* scal, int* ctrl, double* hist, cudaGraphConditionalHandle cond,
+void launch_solve_begin(double* scal, int* ctrl, double* hist, int hstride, int k, const cudaGraphConditionalHandle* cond,
                         cudaStream_t s) {
-  count_launch(); solve_begin_kernel<<<1, 1, 0, s>>>(scal, ctrl, hist, cond);
+  count_launch();
+  if (cond) solve_begin_kernel<true><<<1, 1, 0, s>>>(scal, ctrl, hist, hstride, k, *cond);
+  else solve_begin_kernel<false><<<1, 1, 0, s>>>(scal, ctrl, hist, hstride, k, cudaGraphConditionalHandle{});
 }
-void launch_solve_control(const double* scal, int* ctrl, double* hist, double rtol, int max_iter,
-                          cudaGraphConditionalHandle cond, cudaStream_t s) {
-  count_launch(); solve_control_kernel<<<1, 1, 0, s>>>(scal, ctrl, hist, rtol, max_iter, cond);
+void launch_solve_control(const double* scal, int* ctrl, double* hist, int hstride, int k, double rtol,
+                          int max_iter, const cudaGraphConditionalHandle* cond, cudaStream_t s) {
+  count_launch();
+  if (cond) solve_control_kernel<true><<<1, 1, 0, s>>>(scal, ctrl, hist, hstride, k, rtol, max_iter, *cond);
+  else
+    solve_control_kernel<false><<<1, 1, 0, s>>>(scal, ctrl, hist, hstride, k, rtol, max_iter,
+                                                cudaGraphConditionalHandle{});
 }
 
 // x -= mean(x)   (projection onto range(A) for periodic grids)

@@ -26,6 +26,7 @@ extern std::atomic<unsigned long long> g_launches;
 inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 constexpr int kMaxLevels = 7;     // P <= 32 -> levels P_l = 1, 2, 4, ..., 32
+constexpr int kMaxRhs = 64;       // right-hand sides of one hierarchy (pmg_options.nrhs)
 
 // Launch-shape figures (SM count, resident blocks, kernel attributes) kept per
 // device: a process may drive several GPUs, from several host threads.  with()
@@ -110,7 +111,18 @@ struct FdmAxis {
   const T* W;     // [count][n*n] backward table (diag(w) S)^T, mode-major (times omega on axis 0)
   const T* lam;   // [count][n] eigenvalues in mode order
   const int* sym; // [count] 1: centro-symmetric, tables stored in even-odd folded form
+  // Several right-hand sides stack copies of the grid along its last axis, with walls
+  // between the copies: there, positions come in blocks of bpos (0: no blocks), and
+  // position p starts at start0 + (p - (p / bpos) * bskip) * NP (bskip = 1 for the face
+  // family normal to that axis, whose blocks hold one face more than elements)
+  int bpos;
+  int bskip;
 };
+template <typename T>
+__host__ __device__ __forceinline__ int patch_start(const FdmAxis<T>& ax, int p, int npp) {
+  const int pe = ax.bpos ? p - (p / ax.bpos) * ax.bskip : p;
+  return ax.start0 + pe * npp;
+}
 
 // Largest CTA any patch-kernel launch may use (the autotuner's candidates stay
 // within it; it caps registers at 128 per thread).
@@ -176,6 +188,7 @@ struct CoarseFdm {            // exact global fast-diagonalisation solve at P = 
 // host patch tables along one axis (see FdmAxis): S, W^T, lambda, symmetry flags
 struct AxisTables {
   int n = 0, count = 0, start0 = 0;
+  int bpos = 0, bskip = 0;   // stacked copies (see FdmAxis)
   std::vector<double> S, W, lam;
   std::vector<int> sym;
 };
@@ -198,6 +211,8 @@ struct Hier {
   Grid grid;
   pmg_options opt{};
   int L = 0;                       // finest level index
+  int nrhs = 1;                    // right-hand sides (segments of every level vector)
+  long long n1 = 0;                // finest-level unknowns of one right-hand side
   LevelDims dims[kMaxLevels];
   std::vector<Axis1DHost> axes[kMaxLevels];   // per level, per axis
   int No[kMaxLevels];
@@ -216,7 +231,7 @@ struct Hier {
   double* partial = nullptr;       // reduction partials
   unsigned* counter = nullptr;     // last-block counter
   int* dstatus = nullptr;          // device status word
-  double* hscal = nullptr;         // pinned host mirror of the scalars
+  double* hscal = nullptr;         // pinned host mirror (host_mirror_bytes): control words, results
   double *g_host_stage = nullptr, *u_host_stage = nullptr;   // device buffers for solve_host
   std::vector<void*> owned;
   std::string err;
@@ -245,9 +260,23 @@ struct Hier {
   ApplyTables<dfloat> at_df{};     // finest-level apply tables in double-float (outer_apply DF)
 };
 
-// scalar slots
-// (reductions write two consecutive slots)
+// scalar slots of one segment (right-hand side); reductions write two consecutive slots
 enum { S_DELTA = 0, S_PQ = 2, S_RR = 4, S_ZR = 6, S_ZRO = 7, S_MEAN = 8, S_RR0 = 10, S_NUM = 16 };
+// control words (int) of a solve over k segments: [C_STATUS] global status word (set by
+// kernels whose failure concerns every segment, e.g. the tcgen05 patch kernel's timed-out
+// waits), [C_ITER] iteration counter, [C_ACTIVE] segments still iterating; segment s at
+// kCtrlSeg + 4 s: its status word, iterations, result and active flag (same C_* slots,
+// C_RES the result)
+enum { C_STATUS = 0, C_ITER = 1, C_RES = 2, C_ACTIVE = 3 };
+constexpr int kCtrlSeg = 4;
+// reduction partials of one segment (two per block, at most 152 x 8 blocks)
+constexpr int kPartialStride = 2 * 152 * 8 + 64;
+// pinned host mirror of a hierarchy with k segments: room for the control words or the
+// k solve results
+inline size_t host_mirror_bytes(int k) {
+  const size_t a = sizeof(int) * (size_t)(kCtrlSeg + 4 * k), b = sizeof(SolveResult) * (size_t)k;
+  return (a > b ? a : b) + 64;
+}
 
 // ----------------------------------------------------------------------------
 // set-up (setup.cpp)
@@ -264,6 +293,9 @@ void ec_axis_tables(const Axis1DHost& a, int No, int weighting, double tau, Axis
 void fc_axis_tables(const Axis1DHost& a, int weighting, double tau, AxisTables& t);
 void unfold_tables(AxisTables& t);
 void global_axis_eig(const Axis1DHost& a, std::vector<double>& S, std::vector<double>& lam);
+// k copies of an axis (or of its patch tables) one after the other, separated by walls
+void stack_axis(const Axis1DHost& a, int k, Axis1DHost& out);
+void stack_tables(const AxisTables& t, int k, int skip, AxisTables& out);
 
 // ----------------------------------------------------------------------------
 // kernels (launch wrappers)
@@ -288,20 +320,19 @@ int launch_coarse_fdm(const LevelDims& dm, const CoarseFdm& c, const double* f, 
                       cudaStream_t s, bool cooperative = true);
 template <typename Ta, typename Tb>
 void launch_convert(const Ta* in, Tb* out, long long n, cudaStream_t s);
-void launch_dot(const double* x, const double* y, const double* y2, long long n, double* partial,
+void launch_dot(const double* x, const double* y, const double* y2, long long n, int k, double* partial,
                 unsigned* counter, double* out, int nblocks, cudaStream_t s);
 void launch_cg_update(double* u, double* r, double* r_old, const double* p, const double* q,
-                      const double* scal, int save_old, long long n, double* partial,
-                      unsigned* counter, double* out_rr, int* status, int nblocks, cudaStream_t s,
-                      const int* it_dev = nullptr);
-void launch_p_update(double* p, const double* z, const double* scal, int first, long long n,
-                     cudaStream_t s, const int* it_dev = nullptr);
-void launch_set_delta(double* scal, int* status, cudaStream_t s);
-void launch_solve_begin(double* scal, int* ctrl, double* hist, cudaGraphConditionalHandle cond,
-                        cudaStream_t s);
-void launch_solve_control(const double* scal, int* ctrl, double* hist, double rtol, int max_iter,
-                          cudaGraphConditionalHandle cond, cudaStream_t s);
-void launch_solve_result(const double* scal, const int* ctrl, SolveResult* out, cudaStream_t s);
+                      const double* scal, int save_old, long long n, int k, double* partial,
+                      unsigned* counter, int* ctrl, int nblocks, cudaStream_t s, const int* it_dev = nullptr);
+void launch_p_update(double* p, const double* z, const double* scal, int first, long long n, int k,
+                     cudaStream_t s, const int* it_dev = nullptr, const int* ctrl = nullptr);
+void launch_set_delta(double* scal, int* ctrl, int k, cudaStream_t s);
+void launch_solve_begin(double* scal, int* ctrl, double* hist, int hstride, int k,
+                        const cudaGraphConditionalHandle* cond, cudaStream_t s);
+void launch_solve_control(const double* scal, int* ctrl, double* hist, int hstride, int k, double rtol,
+                          int max_iter, const cudaGraphConditionalHandle* cond, cudaStream_t s);
+void launch_solve_result(const double* scal, const int* ctrl, SolveResult* out, int k, cudaStream_t s);
 void launch_sub_mean(double* x, long long n, double* partial, unsigned* counter, double* scal,
                      int nblocks, cudaStream_t s);
 void launch_mass(const LevelDims& dm, const ApplyTables<double>& at, const double* f, double* g,

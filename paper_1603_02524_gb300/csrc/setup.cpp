@@ -655,3 +655,49 @@ void unfold_tables(AxisTables& t) {
 }
 
 }  // namespace pmg
+
+namespace pmg {
+
+// k copies of a non-periodic axis one after the other: the 1-D operator becomes block
+// diagonal (the wall elements of every copy keep their ghost fold-in and no coupling),
+// so copy c of a vector on the stacked axis is the copy of that vector on the original.
+void stack_axis(const Axis1DHost& a, int k, Axis1DHost& out) {
+  out = a;
+  out.Ne = a.Ne * k;
+  out.dx.clear();
+  out.L0.clear();
+  out.Lm.clear();
+  out.Lp.clear();
+  out.M.clear();
+  out.cpl.clear();
+  for (int c = 0; c < k; ++c) {
+    out.dx.insert(out.dx.end(), a.dx.begin(), a.dx.end());
+    out.L0.insert(out.L0.end(), a.L0.begin(), a.L0.end());
+    out.Lm.insert(out.Lm.end(), a.Lm.begin(), a.Lm.end());
+    out.Lp.insert(out.Lp.end(), a.Lp.begin(), a.Lp.end());
+    out.M.insert(out.M.end(), a.M.begin(), a.M.end());
+    out.cpl.insert(out.cpl.end(), a.cpl.begin(), a.cpl.end());
+  }
+}
+
+// The patch tables of one axis repeated for k stacked copies: the positions of copy c
+// follow those of copy c - 1; skip = 1 where a copy holds one position more than
+// elements (the faces normal to the axis).
+void stack_tables(const AxisTables& t, int k, int skip, AxisTables& out) {
+  out = t;
+  out.count = t.count * k;
+  out.bpos = t.count;
+  out.bskip = skip;
+  out.S.clear();
+  out.W.clear();
+  out.lam.clear();
+  out.sym.clear();
+  for (int c = 0; c < k; ++c) {
+    out.S.insert(out.S.end(), t.S.begin(), t.S.end());
+    out.W.insert(out.W.end(), t.W.begin(), t.W.end());
+    out.lam.insert(out.lam.end(), t.lam.begin(), t.lam.end());
+    out.sym.insert(out.sym.end(), t.sym.begin(), t.sym.end());
+  }
+}
+
+}  // namespace pmg

@@ -130,6 +130,8 @@ FdmAxis<T> upload_axis(std::vector<void*>& owned, const AxisTables& t, const Axi
   ax.n = t.n;
   ax.count = t.count;
   ax.start0 = t.start0;
+  ax.bpos = t.bpos;
+  ax.bskip = t.bskip;
   ax.N = a.Ne * a.NP;
   ax.periodic = a.periodic ? 1 : 0;
   ax.phys = phys;
@@ -473,20 +475,56 @@ void outer_apply(Hier& h, const double* u, const double* f, double* v, cudaStrea
     PMG_CHECK(launch_apply<double>(dm, h.d64[h.L].at, u, f, v, s));
   }
 }
+// Algorithm 2 in three pieces shared by the host-driven solve and the captured one, for
+// all nrhs right-hand sides (segments) of the hierarchy at once; each segment has its
+// own scalars, convergence test and result, the V-cycle and operator applies run on
+// all segments together.
+//   cg_begin:     r = g - A u (periodic: projected), ||r_0|| per segment, r_old = 0
+//   cg_iteration: z = V-cycle(r), beta and p (the first iteration: p = z), delta,
+//                 q = A p, alpha, the u and r updates, the tests ||r|| <= rtol ||r_0||
+//   cg_end:       periodic: zero-mean u; results to res[0..nrhs)
+// A captured solve runs cg_iteration as the body of a device-side `while` node whose
+// condition the tests set (cond); the host-driven solve reads the control words after
+// each iteration and replays the V-cycle from its own graph (direct).
+void cg_begin(Hier& h, const double* g, double* u, const cudaGraphConditionalHandle* cond, cudaStream_t s) {
+  const long long n = h.n1;
+  const int k = h.nrhs, nb = reduce_blocks(n);
+  PMG_CUDA(cudaMemsetAsync(h.dstatus, 0, (kCtrlSeg + 4 * k) * sizeof(int), s));
+  outer_apply(h, u, g, h.r, s);
+  if (h.dims[h.L].periodic) launch_sub_mean(h.r, n, h.partial, h.counter, h.scal, nb, s);   // nrhs = 1
+  launch_dot(h.r, h.r, nullptr, n, k, h.partial, h.counter, h.scal + S_RR0, nb, s);
+  PMG_CUDA(cudaMemsetAsync(h.r_old, 0, (size_t)k * n * sizeof(double), s));
+  launch_solve_begin(h.scal, h.dstatus, h.hist, h.opt.max_iter + 1, k, cond, s);
+}
 
-// Appends one whole MGCG solve of h on (g, u) to `graph` as an independent
-// branch (Algorithm 2): r = g - A u and ||r_0||, then the iterations as a
-// device-side `while` node whose body is z = V-cycle(r), beta and p, q = A p,
-// alpha, the u and r updates and the test ||r|| <= rtol ||r_0||; finally the
-// solve's result is written to *res.  The coarse solve is captured as separate
-// launches, so branches of one graph may run concurrently.  Returns the kernel
-// counts outside the loop and per iteration.
+void cg_iteration(Hier& h, double* u, double rtol, const cudaGraphConditionalHandle* cond, bool direct,
+                  cudaStream_t s) {
+  const long long n = h.n1;
+  const int k = h.nrhs, nb = reduce_blocks(n);
+  const int* it_dev = h.dstatus + C_ITER;
+  if (direct) precondition_graph(h, s);
+  else precondition(h, h.r, h.z, s);
+  launch_dot(h.z, h.r, h.r_old, n, k, h.partial, h.counter, h.scal + S_ZR, nb, s);
+  launch_p_update(h.p, h.z, h.scal, 0, n, k, s, it_dev, h.dstatus);
+  launch_set_delta(h.scal, h.dstatus, k, s);
+  outer_apply(h, h.p, nullptr, h.q, s);
+  launch_dot(h.p, h.q, nullptr, n, k, h.partial, h.counter, h.scal + S_PQ, nb, s);
+  launch_cg_update(u, h.r, h.r_old, h.p, h.q, h.scal, 0, n, k, h.partial, h.counter, h.dstatus, nb, s,
+                   it_dev);
+  launch_solve_control(h.scal, h.dstatus, h.hist, h.opt.max_iter + 1, k, rtol, h.opt.max_iter, cond, s);
+}
+
+void cg_end(Hier& h, double* u, SolveResult* res, cudaStream_t s) {
+  if (h.dims[h.L].periodic) launch_sub_mean(u, h.n1, h.partial, h.counter, h.scal, reduce_blocks(h.n1), s);
+  launch_solve_result(h.scal, h.dstatus, res, h.nrhs, s);
+}
+
+// Appends one whole MGCG solve of h on (g, u) to `graph` as an independent branch:
+// cg_begin, the iterations as a device-side `while` node, cg_end writing res.  The
+// coarse solve is captured as separate launches, so branches of one graph may run
+// concurrently.  Returns the kernel counts outside the loop and per iteration.
 void capture_solve(Hier& h, cudaGraph_t graph, const double* g, double* u, double rtol,
                    SolveResult* res, unsigned long long* fixed, unsigned long long* per_iter) {
-  const int L = h.L;
-  const LevelDims& dm = h.dims[L];
-  const long long n = dm.ndof;
-  const int nb = reduce_blocks(n);
   if (!h.cap_stream) PMG_CUDA(cudaStreamCreateWithFlags(&h.cap_stream, cudaStreamNonBlocking));
   if (!h.cap_stream2) PMG_CUDA(cudaStreamCreateWithFlags(&h.cap_stream2, cudaStreamNonBlocking));
   cudaStream_t cs = h.cap_stream, cb = h.cap_stream2;
@@ -500,12 +538,7 @@ void capture_solve(Hier& h, cudaGraph_t graph, const double* g, double* u, doubl
     PMG_CUDA(cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0,
                                            cudaStreamCaptureModeRelaxed));
     outer = true;
-    PMG_CUDA(cudaMemsetAsync(h.dstatus, 0, 4 * sizeof(int), cs));
-    outer_apply(h, u, g, h.r, cs);
-    if (dm.periodic) launch_sub_mean(h.r, n, h.partial, h.counter, h.scal, nb, cs);
-    launch_dot(h.r, h.r, nullptr, n, h.partial, h.counter, h.scal + S_RR0, nb, cs);
-    PMG_CUDA(cudaMemsetAsync(h.r_old, 0, n * sizeof(double), cs));
-    launch_solve_begin(h.scal, h.dstatus, h.hist, cond, cs);
+    cg_begin(h, g, u, &cond, cs);
     cudaStreamCaptureStatus cst;
     const cudaGraphNode_t* deps = nullptr;
     const cudaGraphEdgeData* edges = nullptr;
@@ -523,23 +556,14 @@ void capture_solve(Hier& h, cudaGraph_t graph, const double* g, double* u, doubl
     PMG_CUDA(cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0,
                                            cudaStreamCaptureModeRelaxed));
     inner = true;
-    precondition(h, h.r, h.z, cb);
-    launch_dot(h.z, h.r, h.r_old, n, h.partial, h.counter, h.scal + S_ZR, nb, cb);
-    launch_p_update(h.p, h.z, h.scal, 0, n, cb, h.dstatus + 1);
-    launch_set_delta(h.scal, h.dstatus, cb);
-    outer_apply(h, h.p, nullptr, h.q, cb);
-    launch_dot(h.p, h.q, nullptr, n, h.partial, h.counter, h.scal + S_PQ, nb, cb);
-    launch_cg_update(u, h.r, h.r_old, h.p, h.q, h.scal, 0, n, h.partial, h.counter, h.scal + S_RR,
-                     h.dstatus, nb, cb, h.dstatus + 1);
-    launch_solve_control(h.scal, h.dstatus, h.hist, rtol, h.opt.max_iter, cond, cb);
+    cg_iteration(h, u, rtol, &cond, false, cb);
     cudaGraph_t body_out = nullptr;
     inner = false;
     PMG_CUDA(cudaStreamEndCapture(cb, &body_out));
     c2 = g_launches.load();
     PMG_CUDA(cudaStreamUpdateCaptureDependencies(cs, &loop, nullptr, 1,
                                                  cudaStreamSetCaptureDependencies));
-    if (dm.periodic) launch_sub_mean(u, n, h.partial, h.counter, h.scal, nb, cs);
-    launch_solve_result(h.scal, h.dstatus, res, cs);
+    cg_end(h, u, res, cs);
     cudaGraph_t out = nullptr;
     outer = false;
     PMG_CUDA(cudaStreamEndCapture(cs, &out));
@@ -581,13 +605,13 @@ void build_solve_graph(Hier& h, const double* g, double* u, double rtol) {
   cudaGetLastError();
 }
 
-void fill_stats(pmg_stats* st, const SolveResult& r, const double* hist, cudaStream_t s) {
+void fill_stats(pmg_stats* st, const SolveResult& r, const double* hist, int device_loop, cudaStream_t s) {
   if (!st) return;
   st->iterations = r.iterations;
   st->r0 = r.r0;
   st->rn = r.rn;
   st->status = r.status;
-  st->device_loop = 1;
+  st->device_loop = device_loop;
   if (st->history) {
     PMG_CUDA(cudaMemcpyAsync(st->history, hist, sizeof(double) * (r.iterations + 1),
                              cudaMemcpyDeviceToHost, s));
@@ -595,23 +619,33 @@ void fill_stats(pmg_stats* st, const SolveResult& r, const double* hist, cudaStr
   }
 }
 
-int solve_graph_run(Hier& h, pmg_stats* st, cudaStream_t s) {
-  PMG_CUDA(cudaGraphLaunch(h.sv_exec, s));
-  PMG_CUDA(cudaMemcpyAsync(h.hscal, h.dres, sizeof(SolveResult), cudaMemcpyDeviceToHost, s));
-  PMG_CUDA(cudaStreamSynchronize(s));
-  SolveResult r;
-  std::memcpy(&r, h.hscal, sizeof r);
-  g_launches.fetch_add(h.sv_fixed + (unsigned long long)r.iterations * h.sv_iter,
-                       std::memory_order_relaxed);
-  fill_stats(st, r, h.hist, s);
-  return r.status;
+// Statistics of the nrhs segments (st: nrhs entries, may be null); returns the status
+// of the first segment that failed, else PMG_OK.
+int report_results(Hier& h, const SolveResult* r, pmg_stats* st, int device_loop, cudaStream_t s) {
+  int first = PMG_OK;
+  for (int sg = 0; sg < h.nrhs; ++sg) {
+    if (st) fill_stats(&st[sg], r[sg], h.hist + (size_t)sg * (h.opt.max_iter + 1), device_loop, s);
+    if (first == PMG_OK && r[sg].status != PMG_OK) first = r[sg].status;
+  }
+  return first;
 }
 
-void read_scalars(Hier& h, cudaStream_t s, int* status) {
-  PMG_CUDA(cudaMemcpyAsync(h.hscal, h.scal, sizeof(double) * S_NUM, cudaMemcpyDeviceToHost, s));
-  PMG_CUDA(cudaMemcpyAsync(h.hscal + S_NUM, h.dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+// Largest iteration count of a solve's segments (the number of loop iterations run).
+int loop_iterations(const SolveResult* r, int k) {
+  int m = 0;
+  for (int sg = 0; sg < k; ++sg) m = r[sg].iterations > m ? r[sg].iterations : m;
+  return m;
+}
+
+int solve_graph_run(Hier& h, pmg_stats* st, cudaStream_t s) {
+  PMG_CUDA(cudaGraphLaunch(h.sv_exec, s));
+  PMG_CUDA(cudaMemcpyAsync(h.hscal, h.dres, sizeof(SolveResult) * h.nrhs, cudaMemcpyDeviceToHost, s));
   PMG_CUDA(cudaStreamSynchronize(s));
-  std::memcpy(status, h.hscal + S_NUM, sizeof(int));
+  std::vector<SolveResult> r(h.nrhs);
+  std::memcpy(r.data(), h.hscal, sizeof(SolveResult) * h.nrhs);
+  g_launches.fetch_add(h.sv_fixed + (unsigned long long)loop_iterations(r.data(), h.nrhs) * h.sv_iter,
+                       std::memory_order_relaxed);
+  return report_results(h, r.data(), st, 1, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -711,65 +745,30 @@ int solve_impl(Hier& h, const double* g, double* u, double rtol, pmg_stats* st, 
       build_solve_graph(h, g, u, rtol);
     if (h.sv_state == 1) return solve_graph_run(h, st, s);
   }
-  const int rc = solve_host_loop(h, g, u, rtol, st, s);
-  if (st) {
-    st->status = rc;
-    st->device_loop = 0;
-  }
-  return rc;
+  return solve_host_loop(h, g, u, rtol, st, s);
 }
 
 int solve_host_loop(Hier& h, const double* g, double* u, double rtol, pmg_stats* st,
                     cudaStream_t s) {
-  const int L = h.L;
-  const LevelDims& dm = h.dims[L];
-  const long long n = dm.ndof;
-  const int nb = reduce_blocks(n);
-  PMG_CUDA(cudaMemsetAsync(h.dstatus, 0, sizeof(int), s));
-  // r = g - A u (fp64); periodic: project onto range(A)
-  outer_apply(h, u, g, h.r, s);
-  if (dm.periodic) launch_sub_mean(h.r, n, h.partial, h.counter, h.scal, nb, s);
-  launch_dot(h.r, h.r, nullptr, n, h.partial, h.counter, h.scal + S_RR0, nb, s);
-  int status = 0;
-  read_scalars(h, s, &status);
-  const double r0 = std::sqrt(h.hscal[S_RR0]);
-  if (st) {
-    st->iterations = 0;
-    st->r0 = r0;
-    st->rn = r0;
-    if (st->history) st->history[0] = r0;
+  const int k = h.nrhs;
+  int* ctrl = reinterpret_cast<int*>(h.hscal);
+  auto read_ctrl = [&] {
+    PMG_CUDA(cudaMemcpyAsync(ctrl, h.dstatus, (kCtrlSeg + 4 * k) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    PMG_CUDA(cudaStreamSynchronize(s));
+  };
+  cg_begin(h, g, u, nullptr, s);
+  read_ctrl();
+  for (int it = 1; it <= h.opt.max_iter && ctrl[C_ACTIVE] > 0; ++it) {
+    cg_iteration(h, u, rtol, nullptr, true, s);
+    read_ctrl();
   }
-  if (!(r0 == r0)) return PMG_ENAN;
-  if (r0 == 0.0) {
-    if (dm.periodic) launch_sub_mean(u, n, h.partial, h.counter, h.scal, nb, s);
-    return PMG_OK;
-  }
-  precondition_graph(h, s);
-  PMG_CUDA(cudaMemcpyAsync(h.p, h.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  launch_dot(h.p, h.r, nullptr, n, h.partial, h.counter, h.scal + S_DELTA, nb, s);
-  int rc = PMG_ENOCONV;
-  for (int it = 1; it <= h.opt.max_iter; ++it) {
-    outer_apply(h, h.p, nullptr, h.q, s);
-    launch_dot(h.p, h.q, nullptr, n, h.partial, h.counter, h.scal + S_PQ, nb, s);
-    launch_cg_update(u, h.r, h.r_old, h.p, h.q, h.scal, it >= 2 ? 1 : 0, n, h.partial, h.counter,
-                     h.scal + S_RR, h.dstatus, nb, s);
-    read_scalars(h, s, &status);
-    const double rn = std::sqrt(h.hscal[S_RR]);
-    if (st) {
-      st->iterations = it;
-      st->rn = rn;
-      if (st->history) st->history[it] = rn;
-    }
-    if (status != 0) { rc = status; break; }
-    if (rn <= rtol * r0) { rc = PMG_OK; break; }
-    precondition_graph(h, s);
-    launch_dot(h.z, h.r, it >= 2 ? h.r_old : nullptr, n, h.partial, h.counter, h.scal + S_ZR, nb, s);
-    launch_p_update(h.p, h.z, h.scal, it == 1 ? 1 : 0, n, s);
-    launch_set_delta(h.scal, h.dstatus, s);
-  }
-  if (dm.periodic) launch_sub_mean(u, n, h.partial, h.counter, h.scal, nb, s);
+  cg_end(h, u, h.dres, s);
+  PMG_CUDA(cudaMemcpyAsync(h.hscal, h.dres, sizeof(SolveResult) * k, cudaMemcpyDeviceToHost, s));
+  PMG_CUDA(cudaStreamSynchronize(s));
+  std::vector<SolveResult> r(k);
+  std::memcpy(r.data(), h.hscal, sizeof(SolveResult) * k);
   PMG_CUDA(cudaGetLastError());
-  return rc;
+  return report_results(h, r.data(), st, 0, s);
 }
 
 // A batch of independent solves captured as one CUDA graph: one branch per
@@ -780,8 +779,9 @@ struct Batch {
   std::vector<double*> u;
   double rtol = 0.0;
   cudaGraphExec_t exec = nullptr;
-  SolveResult* dres = nullptr;     // device [count]
-  SolveResult* hres = nullptr;     // pinned host [count]
+  SolveResult* dres = nullptr;     // device [total segments]
+  SolveResult* hres = nullptr;     // pinned host [total segments]
+  std::vector<int> off;            // first segment of solve i
   std::vector<unsigned long long> fixed, per_iter;
   std::vector<void*> owned;
   std::string err;
@@ -845,6 +845,7 @@ void pmg_options_default(pmg_options* opt) {
   opt->precision = PMG_PREC_FP64;
   opt->max_iter = 100;
   for (int l = 0; l < 8; ++l) opt->omega_level[l] = opt->tau_level[l] = 0.0;
+  opt->nrhs = 1;
   opt->preconditioner = PMG_PC_VCYCLE;
   opt->outer_apply = PMG_OUTER_FP64;
 }
@@ -911,6 +912,8 @@ int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
     return PMG_EINVAL;
   if (o.preconditioner != PMG_PC_VCYCLE && o.preconditioner != PMG_PC_NONE) return PMG_EINVAL;
   if (o.outer_apply != PMG_OUTER_FP64 && o.outer_apply != PMG_OUTER_DF) return PMG_EINVAL;
+  // several right-hand sides stack copies of the grid along its last axis, separated by walls
+  if (o.nrhs < 1 || o.nrhs > kMaxRhs || (o.nrhs > 1 && gr->bc_periodic)) return PMG_EINVAL;
   Hier* h = nullptr;
   try {
     h = new Hier();
@@ -919,6 +922,8 @@ int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
   }
   h->grid = *gr;
   h->opt = o;
+  const int k = o.nrhs;
+  h->nrhs = k;
   int L = 0;
   while ((1 << L) < gr->P) ++L;
   h->L = L;
@@ -939,18 +944,35 @@ int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
         dm.ne[d] = gr->ne[d];
         dm.nelem *= gr->ne[d];
       }
+      // several right-hand sides: k copies of the grid stacked along its last axis
+      // with walls between them, so every level vector holds the k vectors back to back
+      dm.ne[dim - 1] *= k;
+      dm.nelem *= k;
       dm.ndof = dm.nelem * dm.NP * dm.NP * dm.NPz;
       dm.periodic = gr->bc_periodic;
       h->axes[l].resize(dim);
-      for (int d = 0; d < dim; ++d)
-        build_axis(h->axes[l][d], Pl, gr->spacing[d], gr->bc_periodic != 0, gr->beta[d], gr->mu_star);
+      std::vector<Axis1DHost> single(dim);
+      for (int d = 0; d < dim; ++d) {
+        build_axis(single[d], Pl, gr->spacing[d], gr->bc_periodic != 0, gr->beta[d], gr->mu_star);
+        if (k > 1 && d == dim - 1) stack_axis(single[d], k, h->axes[l][d]);
+        else h->axes[l][d] = single[d];
+      }
       h->No[l] = overlap_nodes(Pl, o.overlap);
       std::vector<AxisTables> ec(dim), fc(dim);
       if (l > 0) {
         for (int d = 0; d < dim; ++d) {
-          ec_axis_tables(h->axes[l][d], h->No[l], o.weighting, level_tau(o, l), ec[d]);
+          ec_axis_tables(single[d], h->No[l], o.weighting, level_tau(o, l), ec[d]);
           if (o.smoother == PMG_SMOOTHER_FA) {
-            fc_axis_tables(h->axes[l][d], o.weighting, level_tau(o, l), fc[d]);
+            fc_axis_tables(single[d], o.weighting, level_tau(o, l), fc[d]);
+          }
+          if (k > 1 && d == dim - 1) {
+            AxisTables t;
+            stack_tables(ec[d], k, 0, t);
+            ec[d] = t;
+            if (o.smoother == PMG_SMOOTHER_FA) {
+              stack_tables(fc[d], k, 1, t);
+              fc[d] = t;
+            }
           }
         }
       }
@@ -984,21 +1006,22 @@ int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
     c.tmp[0] = dev_alloc<double>(h->owned, h->dims[0].ndof);
     c.tmp[1] = dev_alloc<double>(h->owned, h->dims[0].ndof);
     const long long n = h->dims[L].ndof;
+    h->n1 = n / k;
     h->r = dev_alloc<double>(h->owned, n);
     h->r_old = dev_alloc<double>(h->owned, n);
     h->p = dev_alloc<double>(h->owned, n);
     h->q = dev_alloc<double>(h->owned, n);
     h->z = dev_alloc<double>(h->owned, n);
-    h->scal = dev_alloc<double>(h->owned, S_NUM);
-    h->partial = dev_alloc<double>(h->owned, 2 * 152 * 8 + 64);
-    h->counter = dev_alloc<unsigned>(h->owned, 4);
-    h->dstatus = dev_alloc<int>(h->owned, 4);
-    h->hist = dev_alloc<double>(h->owned, (size_t)o.max_iter + 1);
-    h->dres = dev_alloc<SolveResult>(h->owned, 1);
-    PMG_CUDA(cudaMemset(h->counter, 0, 4 * sizeof(unsigned)));
-    PMG_CUDA(cudaMemset(h->dstatus, 0, 4 * sizeof(int)));
-    PMG_CUDA(cudaMemset(h->scal, 0, S_NUM * sizeof(double)));
-    PMG_CUDA(cudaMallocHost(&h->hscal, sizeof(double) * (S_NUM + 2)));
+    h->scal = dev_alloc<double>(h->owned, (size_t)S_NUM * k);
+    h->partial = dev_alloc<double>(h->owned, (size_t)kPartialStride * k);
+    h->counter = dev_alloc<unsigned>(h->owned, k);
+    h->dstatus = dev_alloc<int>(h->owned, kCtrlSeg + 4 * k);
+    h->hist = dev_alloc<double>(h->owned, (size_t)(o.max_iter + 1) * k);
+    h->dres = dev_alloc<SolveResult>(h->owned, k);
+    PMG_CUDA(cudaMemset(h->counter, 0, k * sizeof(unsigned)));
+    PMG_CUDA(cudaMemset(h->dstatus, 0, (kCtrlSeg + 4 * k) * sizeof(int)));
+    PMG_CUDA(cudaMemset(h->scal, 0, (size_t)S_NUM * k * sizeof(double)));
+    PMG_CUDA(cudaMallocHost(&h->hscal, host_mirror_bytes(k)));
     // patch kernels that can detect a failed bounded wait report it in the hierarchy's
     // status word, which pmg_solve reads (and pmg_device_status for the other calls)
     for (int l = 1; l <= L; ++l) {
@@ -1186,11 +1209,16 @@ int pmg_batch_create(int count, const pmg_hier* hiers, const double* const* g_de
       precondition_graph(*h, 0);
     }
     PMG_CUDA(cudaStreamSynchronize(0));
-    b->dres = dev_alloc<SolveResult>(b->owned, count);
-    PMG_CUDA(cudaMallocHost(&b->hres, sizeof(SolveResult) * count));
+    int total = 0;
+    for (Hier* h : hs) {
+      b->off.push_back(total);
+      total += h->nrhs;
+    }
+    b->dres = dev_alloc<SolveResult>(b->owned, total);
+    PMG_CUDA(cudaMallocHost(&b->hres, sizeof(SolveResult) * total));
     PMG_CUDA(cudaGraphCreate(&graph, 0));
     for (int i = 0; i < count; ++i)
-      capture_solve(*hs[i], graph, b->g[i], b->u[i], rtol, b->dres + i, &b->fixed[i],
+      capture_solve(*hs[i], graph, b->g[i], b->u[i], rtol, b->dres + b->off[i], &b->fixed[i],
                     &b->per_iter[i]);
     PMG_CUDA(cudaGraphInstantiate(&b->exec, graph, 0));
   } catch (const CudaError& e) {
@@ -1215,18 +1243,19 @@ int pmg_batch_solve(pmg_batch bb, pmg_stats* stats, void* stream) {
   if (!b) return PMG_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const int count = (int)b->h.size();
+  const int total = b->off[count - 1] + b->h[count - 1]->nrhs;
   int first_bad = PMG_OK;
   try {
     PMG_CUDA(cudaGraphLaunch(b->exec, s));
-    PMG_CUDA(cudaMemcpyAsync(b->hres, b->dres, sizeof(SolveResult) * count,
+    PMG_CUDA(cudaMemcpyAsync(b->hres, b->dres, sizeof(SolveResult) * total,
                              cudaMemcpyDeviceToHost, s));
     PMG_CUDA(cudaStreamSynchronize(s));
     for (int i = 0; i < count; ++i) {
-      const SolveResult& r = b->hres[i];
-      g_launches.fetch_add(b->fixed[i] + (unsigned long long)r.iterations * b->per_iter[i],
+      const SolveResult* r = b->hres + b->off[i];
+      g_launches.fetch_add(b->fixed[i] + (unsigned long long)loop_iterations(r, b->h[i]->nrhs) * b->per_iter[i],
                            std::memory_order_relaxed);
-      if (stats) fill_stats(&stats[i], r, b->h[i]->hist, s);
-      if (first_bad == PMG_OK && r.status != PMG_OK) first_bad = r.status;
+      const int st = report_results(*b->h[i], r, stats ? stats + b->off[i] : nullptr, 1, s);
+      if (first_bad == PMG_OK && st != PMG_OK) first_bad = st;
     }
   } catch (const CudaError& e) {
     b->err = e.msg;
@@ -1308,10 +1337,10 @@ int pmg_device_status(pmg_hier hh, void* stream, int* status) {
   return guarded(h, [&] {
     cudaStream_t s = (cudaStream_t)stream;
     int v = 0;
-    PMG_CUDA(cudaMemcpyAsync(h->hscal + S_NUM, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PMG_CUDA(cudaMemcpyAsync(h->hscal, h->dstatus + C_STATUS, sizeof(int), cudaMemcpyDeviceToHost, s));
     PMG_CUDA(cudaStreamSynchronize(s));
-    std::memcpy(&v, h->hscal + S_NUM, sizeof(int));
-    PMG_CUDA(cudaMemsetAsync(h->dstatus, 0, sizeof(int), s));
+    std::memcpy(&v, h->hscal, sizeof(int));
+    PMG_CUDA(cudaMemsetAsync(h->dstatus + C_STATUS, 0, sizeof(int), s));
     PMG_CUDA(cudaStreamSynchronize(s));
     *status = v;
     return (int)PMG_OK;

@@ -2,10 +2,10 @@
 patch solve as tf32 MMAs, accumulators in tensor memory) against the FP64 oracle.
 
 Tolerance of one smoothing step, relative to the max-norm of the oracle's correction:
-every operand of a line pass is rounded to tf32 (11 significant bits, relative error
-<= 2^-11 = 4.9e-4; the gathered residual is truncated, <= 2^-10) and the products are
-summed in fp32; six passes and the scaling compound to a few 2^-11, so 1e-2 bounds the
-step with margin while any misplaced row,
+the tables are rounded to tf32 (11 significant bits, relative error <= 2^-11 = 4.9e-4),
+the gathered residual and the operands between line passes truncated to tf32 (< 2^-10),
+and the products summed in fp32; six passes and the scaling compound to a few 2^-10, so
+1e-2 bounds the step with margin while any misplaced row,
 column or table entry gives errors of order 1.  The fp32 residual of the smoother adds
 ~1e-7.  The full MGCG solve (FP64 flexible CG, tf32 V-cycle) must reach the oracle's
 solution to 1e-9 with at most two more iterations than the oracle.  Every test also
