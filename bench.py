@@ -77,11 +77,14 @@ def parse():
                     help="arithmetic of the timed solve's V-cycle (the outer CG is always FP64); "
                          "default fp64, mixed_tf32 for the batched workload c5")
     ap.add_argument("--autotune", action="store_true",
-                    help="autotune the patch kernel's CTA size before timing (always on for c5)")
+                    help="autotune the patch kernels' CTA sizes before timing (the default)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the patch kernels with their default CTA sizes")
     ap.add_argument("--outer-apply", default=None, choices=["fp64", "df"],
                     help="arithmetic of the CG's own operator apply: FP64, or double-float on the FP32 "
                          "pipes; default fp64, df for the batched workload c5")
     args = ap.parse_args()
+    args.autotune = not args.no_autotune
     if args.precision is None:
         args.precision = "mixed_tf32" if args.workload == "c5" else "fp64"
     if args.outer_apply is None:
@@ -332,19 +335,22 @@ def main_batch(args):
     lib = binding.load()
     members = syn.config5()
     t0 = time.perf_counter()
+    # one hierarchy per grid carrying its right-hand sides (pmg_options.nrhs): the tables
+    # and every kernel launch are shared by the grid's right-hand sides
     grids, hiers, gs, us = [], [], [], []
     for w in members:
         grid = Grid(w.dim, w.P, w.n_elem, w.spacing, periodic=w.periodic, mu_star=w.mu_star, beta=w.beta)
         grids.append(grid)
-        for k in range(w.extra["n_rhs"]):
-            h = Hierarchy(grid, precision=args.precision, outer_apply=args.outer_apply, **BATCH_OPTS)
-            f = syn.gauss_noise(w, seed=w.seed * 8 + k)
-            ft = torch.from_numpy(np.ascontiguousarray(f).reshape(-1)).to(dev)
-            g = torch.empty_like(ft)
-            h.rhs(ft, g)
-            hiers.append(h)
-            gs.append(g)
-            us.append(torch.zeros_like(g))
+        k = w.extra["n_rhs"]
+        h = Hierarchy(grid, precision=args.precision, outer_apply=args.outer_apply, nrhs=k, **BATCH_OPTS)
+        f = np.concatenate([np.ascontiguousarray(syn.gauss_noise(w, seed=w.seed * 8 + i)).reshape(-1)
+                            for i in range(k)])
+        ft = torch.from_numpy(f).to(dev)
+        g = torch.empty_like(ft)
+        h.rhs(ft, g)
+        hiers.append(h)
+        gs.append(g)
+        us.append(torch.zeros_like(g))
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     for h in hiers:                      # tile (CTA) sizes per patch shape, cached per shape
@@ -386,11 +392,13 @@ def main_batch(args):
     barrier(world)
     t_step = max_over_ranks(statistics.mean(times), world, dev)
     its = [r[1] for r in res]
+    n_solves = len(res)
     line = {"metric": METRIC, "value": world * total / (t_step * 1e-3), "unit": "DOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[(args.precision, args.outer_apply)], "data": "synthetic",
-            "config": {"workload": BATCH_NAME, "solves": len(hiers),
+            "config": {"workload": BATCH_NAME, "solves": n_solves, "hierarchies": len(hiers),
+                       "rhs_per_hierarchy": members[0].extra["n_rhs"],
                        "grids": len(members), "total_dof": total, "max_dof": max(ndof), "min_dof": min(ndof),
                        "smoother": "FA_l variable V", "precision": args.precision,
                        "outer_apply": args.outer_apply, "rtol": 1e-10,
@@ -400,29 +408,47 @@ def main_batch(args):
                        "parallelism": f"replicas{world}"},
             "gpu_launches": int(launches), "clocks": clk}
     if not args.no_extras:
-        # the same solves one after another (each a captured single solve) on the same stream
-        for h, g, u in zip(hiers, gs, us):
-            u.zero_()
-            h.solve(g, u, rtol=1e-10, history=False)
+        # the same right-hand sides solved one after another, each on a single-right-hand-side
+        # hierarchy of its grid (a captured single solve each), on the same stream
+        singles = []
+        for w, grid, g in zip(members, grids, gs):
+            n1 = g.numel() // w.extra["n_rhs"]
+            for i in range(w.extra["n_rhs"]):
+                hs1 = Hierarchy(grid, precision=args.precision, outer_apply=args.outer_apply, **BATCH_OPTS)
+                hs1.autotune()
+                singles.append((hs1, g[i * n1:(i + 1) * n1], torch.zeros(n1, dtype=torch.float64, device=dev)))
+        for hs1, g1, u1 in singles:
+            hs1.solve(g1, u1, rtol=1e-10, history=False)
         torch.cuda.synchronize()
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        for u in us:
-            u.zero_()
+        for _, _, u1 in singles:
+            u1.zero_()
         e0.record(stream)
-        for h, g, u in zip(hiers, gs, us):
-            h.solve(g, u, rtol=1e-10, history=False)
+        for hs1, g1, u1 in singles:
+            hs1.solve(g1, u1, rtol=1e-10, history=False)
         e1.record(stream)
         e1.synchronize()
         t_seq = e0.elapsed_time(e1)
+        dmax = 0.0
+        for (w, u), k0 in zip(zip(members, us), range(0, len(singles), members[0].extra["n_rhs"])):
+            n1 = u.numel() // w.extra["n_rhs"]
+            for i in range(w.extra["n_rhs"]):
+                u1 = singles[k0 + i][2]
+                dmax = max(dmax, float((u[i * n1:(i + 1) * n1] - u1).abs().max() / u1.abs().max()))
         line["sequential"] = {"ms": t_seq, "value": total / (t_seq * 1e-3), "unit": "DOF/s",
-                              "batch_speedup": t_seq / t_step,
-                              "note": "the same solves issued one after another (pmg_solve each)"}
+                              "batch_speedup": t_seq / t_step, "solves": len(singles),
+                              "max_rel_diff_vs_batch": dmax,
+                              "note": "the same right-hand sides solved one after another, each on its own "
+                                      "single-right-hand-side hierarchy (pmg_solve each)"}
+        for hs1, _, _ in singles:
+            hs1.close()
+        del singles
         # dominant kernel: the FA patch sweep on the finest level of the largest member
         big = max(range(len(hiers)), key=lambda i: ndof[i])
         hb = hiers[big]
-        wb = members[[i for i, w in enumerate(members) for _ in range(w.extra["n_rhs"])][big]]
+        wb = members[big]
 
         def native():
             st = lib.pmg_schwarz_sweep_native(hb.handle, hb.L, 0, binding._stream(stream))
@@ -653,6 +679,8 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
     for other in others:
         prec, outer = VARIANTS[other]
         hm = Hierarchy(grid, precision=prec, outer_apply=outer, **opts)
+        if args.autotune:
+            hm.autotune()
         um = torch.zeros_like(g)
         hm.solve(g, um, rtol=1e-10, history=False)
         tm, itm = [], 0
@@ -695,7 +723,10 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
         net, hist, _ = learned.train_default()
         t_train = time.perf_counter() - t0
         om, ta = net.level_params(w.P, w.spacing)
-        hl = Hierarchy(grid, precision=args.precision, omega_level=om, tau_level=ta, **opts)
+        hl = Hierarchy(grid, precision=args.precision, outer_apply=args.outer_apply, omega_level=om,
+                       tau_level=ta, **opts)
+        if args.autotune:
+            hl.autotune()
         ul = torch.zeros_like(g)
         hl.solve(g, ul, rtol=1e-10, history=False)
         tl, itl = [], 0
