@@ -5,7 +5,11 @@ CUDA kernels pmg_mlp_forward / pmg_mlp_backward / pmg_mlp_adam) maps the feature
 of one p-level of a hierarchy
 
     x = [log2 P_l, N_o,l, a_1, a_2, a_3, l / L],
-    a_1 >= a_2 >= a_3 = 0: log2 of each axis' median element width over the smallest,
+    a_1 >= a_2 >= a_3 = 0: the element aspect ratios, as 90th percentiles over the
+    elements of the sorted log2 ratios of an element's three widths to its smallest
+    (on a grid of uniform widths per axis every element has the same ratios; on a
+    graded grid the percentile weights the most stretched elements, which limit the
+    smoother),
 
 to two raw outputs, turned into the level's smoother parameters
 
@@ -17,7 +21,11 @@ Training targets come from the method's own runs: for each generated grid the MG
 residual-reduction rate rho = (r_n / r_0)^(1/n) is measured for a set of candidate
 (omega, tau) pairs, and the best pair with omega <= 1.3 that is robust to a
 +-0.1 error in omega (see robust_best) becomes the target of every level of that
-grid; samples are weighted by the rate gain over the paper's parameters.
+grid; samples are weighted by the rate gain over the paper's parameters.  The
+generated grids are 4^3 elements, uniform per axis with aspect ratios 1..32 or graded
+geometrically along two axes (width ratios up to 32, the shape of the stretched
+64 x 16 x 8 workload), solved with the face-centred smoother and the variable V-cycle
+that the stretched and the batched workloads use.
 """
 from __future__ import annotations
 
@@ -43,10 +51,14 @@ def overlap_nodes(P_l: int, policy: str = "l") -> int:
 
 
 def aspect_features(spacing) -> list:
-    med = [float(np.median(s)) for s in spacing] + [None] * (3 - len(spacing))
-    hs = [m for m in med if m is not None]
-    hmin = min(hs)
-    a = sorted((math.log2(m / hmin) for m in hs), reverse=True)
+    """90th percentiles over the elements of the sorted log2 width ratios (see above)."""
+    ws = [np.asarray(s, dtype=np.float64) for s in spacing]
+    while len(ws) < 3:
+        ws.append(None)
+    grids = np.meshgrid(*[w for w in ws if w is not None], indexing="ij")
+    h = np.stack([g.reshape(-1) for g in grids], axis=1)           # elements x dims
+    r = np.sort(np.log2(h / h.min(axis=1, keepdims=True)), axis=1)[:, ::-1]
+    a = [float(np.percentile(r[:, d], 90)) for d in range(r.shape[1])]
     return (a + [0.0, 0.0, 0.0])[:3]
 
 
@@ -165,9 +177,19 @@ class GridConfig:
     aspect: tuple                    # element width ratios hx : hy : hz
     smoother: str = "FA"
     periodic: bool = False
+    grading: tuple = (1, 1, 1)       # per axis: largest / smallest width of a geometric grading
+    variable_v: bool = True
 
     def spacing(self):
-        return [[a / n] * n for a, n in zip(self.aspect, self.n_elem)]
+        out = []
+        for a, n, q in zip(self.aspect, self.n_elem, self.grading):
+            if q == 1 or n == 1:
+                out.append([a / n] * n)
+            else:
+                r = q ** (1.0 / (n - 1))
+                w = [a * r ** k for k in range(n)]
+                out.append([x / n for x in w])
+        return out
 
 
 def measure_rate(cfg: GridConfig, omega_level=None, tau_level=None, iters=8, seed=0):
@@ -175,7 +197,7 @@ def measure_rate(cfg: GridConfig, omega_level=None, tau_level=None, iters=8, see
     import torch
     g = Grid(3, cfg.P, cfg.n_elem, cfg.spacing(), periodic=cfg.periodic)
     h = Hierarchy(g, smoother=cfg.smoother, overlap="l", max_iter=iters, omega_level=omega_level,
-                  tau_level=tau_level)
+                  tau_level=tau_level, variable_v=cfg.variable_v)
     n = h.ndof()
     gen = torch.Generator(device="cuda").manual_seed(seed)
     f = torch.rand(n, dtype=torch.float64, device="cuda", generator=gen) * 2 - 1
@@ -218,11 +240,20 @@ def robust_best(rates):
 
 TRAIN_ASPECTS = [(1, 1, 1), (2, 1, 1), (8, 1, 1), (32, 1, 1), (8, 8, 1), (32, 32, 1), (16, 4, 1), (4, 2, 1)]
 HELDOUT_ASPECTS = [(4, 1, 1), (16, 1, 1), (4, 4, 1), (32, 8, 1), (16, 16, 1), (8, 2, 1)]
+# graded grids: x uniform, y and z widths growing geometrically by these total ratios
+TRAIN_GRADINGS = [(1, 4, 4), (1, 16, 16), (1, 32, 32), (1, 8, 32)]
+HELDOUT_GRADINGS = [(1, 32, 8), (1, 16, 4)]
+
+
+def default_configs(P_values=(2, 4, 8), aspects=TRAIN_ASPECTS, gradings=TRAIN_GRADINGS):
+    return ([GridConfig(P, (4, 4, 4), a) for P in P_values for a in aspects]
+            + [GridConfig(P, (4, 4, 4), (1, 1, 1), grading=q) for P in P_values for q in gradings])
 
 
 def train_default(P_values=(2, 4, 8), steps=1500, seed=0, iters=8):
-    """Generate the training grids (FA, 4^3 elements), measure, train a fresh network."""
-    configs = [GridConfig(P, (4, 4, 4), a) for P in P_values for a in TRAIN_ASPECTS]
+    """Generate the training grids (FA with the variable V-cycle, 4^3 elements), measure,
+    train a fresh network."""
+    configs = default_configs(P_values)
     X, T, W, records = make_dataset(configs, iters=iters)
     net = SmootherMLP(init_theta(seed))
     hist = net.train(X, T, W, steps=steps)

@@ -52,26 +52,26 @@ def test_mlp_training_reduces_loss():
 
 
 def test_learned_parameters_beat_paper_parameters_on_heldout_grids(capsys):
-    """Train the MLP on rates measured by the library's own MGCG runs (FA smoother, 4^3
-    elements, P = 2, 4, 8, training aspect ratios), then compare, on held-out aspect
-    ratios, the measured rate with the network's per-level (omega, tau) against the
-    paper's omega = tau = 1."""
+    """Train the MLP on rates measured by the library's own MGCG runs (FA smoother with the
+    variable V-cycle, 4^3 elements, P = 2, 4, 8, training aspect ratios and gradings), then
+    compare, on held-out aspect ratios and gradings, the measured rate with the network's
+    per-level (omega, tau) against the paper's omega = tau = 1."""
     import math
 
     from paper_1603_02524_gb300 import learned
     net, hist, records = learned.train_default()
     assert hist[-1] < 0.5 * hist[0]
     gains, rows = [], []
-    for P in (2, 4, 8):
-        for a in learned.HELDOUT_ASPECTS:
-            cfg = learned.GridConfig(P, (4, 4, 4), a)
-            om, ta = net.level_params(P, cfg.spacing())
-            paper = learned.measure_rate(cfg)
-            mlp = learned.measure_rate(cfg, om, ta)
-            gains.append(math.log(paper / mlp))
-            rows.append((P, a, paper, mlp, om[1:], ta[1:]))
-            # never clearly worse than the paper's parameters on a held-out grid
-            assert mlp <= 1.10 * paper, rows[-1]
+    held = learned.default_configs((2, 4, 8), learned.HELDOUT_ASPECTS, learned.HELDOUT_GRADINGS)
+    for cfg in held:
+        shape = cfg.aspect if cfg.grading == (1, 1, 1) else ("graded",) + tuple(cfg.grading)
+        om, ta = net.level_params(cfg.P, cfg.spacing())
+        paper = learned.measure_rate(cfg)
+        mlp = learned.measure_rate(cfg, om, ta)
+        gains.append(math.log(paper / mlp))
+        rows.append((cfg.P, shape, paper, mlp, om[1:], ta[1:]))
+        # never clearly worse than the paper's parameters on a held-out grid
+        assert mlp <= 1.10 * paper, rows[-1]
     mean_gain = sum(gains) / len(gains)
     with capsys.disabled():
         for P, a, paper, mlp, om, ta in rows:
