@@ -76,26 +76,16 @@ struct TcGeom {
   }
   static constexpr uint32_t OFF_OFF = tab_off(5) + tbytes(NC);
   static constexpr int NOFF = (NA + NB + NC + 1) / 2 * 2;
-  static constexpr uint32_t ROW_OFF = OFF_OFF + 8u * NOFF;
-  static constexpr uint32_t LAM_OFF = ROW_OFF + 8u * (uint32_t)((NB * NC + 1) / 2 * 2);
+  static constexpr uint32_t LAM_OFF = OFF_OFF + 8u * NOFF;
   // mbarrier of the MMA completions (+0), tensor-memory address slot (+8), and a
   // second mbarrier that nothing ever completes (+16): the stalled-wait test hook
-  static constexpr uint32_t RDST_OFF = (LAM_OFF + 4u * (NA + NB + NC) + 15) / 16 * 16;
-  static constexpr uint32_t BAR_OFF = (RDST_OFF + 4u * NB * NC + 15) / 16 * 16;
+  static constexpr uint32_t BAR_OFF = (LAM_OFF + 4u * (NA + NB + NC) + 15) / 16 * 16;
   static constexpr uint32_t BYTES = BAR_OFF + 32;
   __host__ __device__ static constexpr uint32_t cols(int n, int m) { return (uint32_t)mt(m) * (uint32_t)npd(n); }
   static constexpr uint32_t COLS_USED = mx(mx(cols(NA, M0), cols(NB, M1)), mx(cols(NC, M2), cols(NB, M4)));
   static constexpr uint32_t TCOLS = COLS_USED <= 32 ? 32 : COLS_USED <= 64 ? 64 : COLS_USED <= 128 ? 128 : 256;
   static_assert(COLS_USED <= 256, "accumulators exceed the tensor-memory budget of one CTA");
   static_assert(NA <= 32 && NB <= 32 && NC <= 32 && NC > 1, "tensor-core patch kernel: 3-D, n <= 32");
-};
-
-// Gather and scatter walk the patch rows (fixed b, c) with one lane per node a:
-// R rows per warp, W = 32 / R lanes per row.
-template <int NA>
-struct TcRows {
-  static constexpr int R = NA <= 16 ? 2 : 1;
-  static constexpr int W = 32 / R;
 };
 
 // Table of the patch (forward S or backward W^T, n x n, entry [k][j] = input k,
@@ -243,8 +233,6 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
 #pragma unroll
   for (int i = 0; i < 6; ++i) Tb[i] = reinterpret_cast<float*>(tc_smem + G::tab_off(i));
   long long* off = reinterpret_cast<long long*>(tc_smem + G::OFF_OFF);
-  long long* rowoff = reinterpret_cast<long long*>(tc_smem + G::ROW_OFF);
-  int* rowdst = reinterpret_cast<int*>(tc_smem + G::RDST_OFF);
   float* la = reinterpret_cast<float*>(tc_smem + G::LAM_OFF);
   float* lb = la + NA;
   float* lc = lb + NB;
@@ -256,10 +244,6 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
 
   // operand pads must hold finite values (their products with the zero table pads vanish)
   for (int i = tid; i < (int)(G::OFF_OFF / 4); i += blockDim.x) A[i] = 0.0f;
-  for (int row = tid; row < NB * NC; row += blockDim.x) {
-    const int b = row % NB, c = row / NB, m = b + G::NBP * c;
-    rowdst[row] = (m >> 3) * (int)(G::sbo(NA) / 4) + (m & 7) * 4;
-  }
   if (tid == 0) {
     umma::mbar_init(mbar, 1);
     umma::mbar_init(never, 1);
@@ -288,7 +272,7 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
   const int chunk = (fam.count_total + gridDim.x - 1) / gridDim.x;
   const int pbeg = blockIdx.x * chunk;
   const int pend = min(fam.count_total, pbeg + chunk);
-  int prev[3] = {-1, -1, -1};
+  int prev[3] = {-1, -1, -1}, prevtab[3] = {-1, -1, -1};
   for (int pid = pbeg; pid < pend && ok; ++pid) {
     const int pidx[3] = {pid % ca, (pid / ca) % cb, pid / (ca * cb)};
     const bool fresh[3] = {pidx[0] != prev[0], pidx[1] != prev[1], pidx[2] != prev[2]};
@@ -298,18 +282,24 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
       const FdmAxis<float>& ax = fam.ax[q];
       const int n = nq[q];
       const size_t p = pidx[q];
-      if (q == 0) {
-        tc_table_async<NA, NB, NC, NA>(Tb[0], ax.S + p * NA * NA);
-        tc_table_async<NA, NB, NC, NA>(Tb[1], ax.W + p * NA * NA);
-      } else if (q == 1) {
-        tc_table_async<NA, NB, NC, NB>(Tb[2], ax.S + p * NB * NB);
-        tc_table_async<NA, NB, NC, NB>(Tb[3], ax.W + p * NB * NB);
-      } else {
-        tc_table_async<NA, NB, NC, NC>(Tb[4], ax.S + p * NC * NC);
-        tc_table_async<NA, NB, NC, NC>(Tb[5], ax.W + p * NC * NC);
+      // tables and eigenvalues only when they differ from the ones in shared memory
+      const int tab = ax.tabid ? __ldg(ax.tabid + p) : (int)p;
+      const bool newtab = tab != prevtab[q];
+      prevtab[q] = tab;
+      if (newtab) {
+        if (q == 0) {
+          tc_table_async<NA, NB, NC, NA>(Tb[0], ax.S + p * NA * NA);
+          tc_table_async<NA, NB, NC, NA>(Tb[1], ax.W + p * NA * NA);
+        } else if (q == 1) {
+          tc_table_async<NA, NB, NC, NB>(Tb[2], ax.S + p * NB * NB);
+          tc_table_async<NA, NB, NC, NB>(Tb[3], ax.W + p * NB * NB);
+        } else {
+          tc_table_async<NA, NB, NC, NC>(Tb[4], ax.S + p * NC * NC);
+          tc_table_async<NA, NB, NC, NC>(Tb[5], ax.W + p * NC * NC);
+        }
       }
       for (int a = tid; a < n; a += blockDim.x) {
-        cp_async<4>(lq[q] + a, ax.lam + p * n + a, true);
+        if (newtab) cp_async<4>(lq[q] + a, ax.lam + p * n + a, true);
         const int ph = ax.phys;
         const int npp = (ph == 2) ? dm.NPz : dm.NP;
         int Gi = patch_start(ax, (int)p, npp) + a;
@@ -327,39 +317,20 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
       }
     }
     __syncthreads();
-    if (fresh[1] || fresh[2])
-      for (int rr = tid; rr < NB * NC; rr += blockDim.x) rowoff[rr] = off[NA + rr % NB] + off[NA + NB + rr / NB];
-    __syncthreads();
-    // gather into the first operand (row b + NBP c, K index a; the row's offset in the
-    // operand from the per-CTA table rowdst) as asynchronous copies, zero-filled
-    // outside the grid, one warp per patch row (lane = a); one wait for gather,
-    // tables and eigenvalues.  The tensor core reads the fp32 values
-    // truncated to tf32.
+    // gather into the first operand (row b + NBP c, K index a) as asynchronous copies,
+    // zero-filled outside the grid: each thread takes one (a, c) line and walks b (the
+    // row's offset in the operand is then a compile-time step, the global offset one
+    // broadcast load); lanes hold consecutive a, so a warp's copies are contiguous
     {
-      const int hw = (threadIdx.x & 31) / TcRows<NA>::W, lane = (threadIdx.x & 31) % TcRows<NA>::W;
-      const int rstep = (blockDim.x >> 5) * TcRows<NA>::R;
-      const long long oa = lane < NA ? off[lane] : 0;
-      const int lk = (lane >> 2) * 36 + (lane & 3);
-      // four rows per step: their row offsets are read before the first copy is issued
-      for (int row0 = (tid >> 5) * TcRows<NA>::R + hw; row0 < NB * NC; row0 += 4 * rstep) {
-        long long ro[4];
+      constexpr int S = (int)G::sbo(NA) / 4;
+      for (int pr = tid; pr < NA * NC; pr += blockDim.x) {
+        const int a = pr % NA, c = pr / NA;
+        const long long oac = off[a] + off[NA + NB + c];
+        const int dac = c * (G::NBP / 8) * S + (a >> 2) * 36 + (a & 3);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int row = row0 + i * rstep;
-          ro[i] = row < NB * NC ? rowoff[row] : kInvalidOffset;
-        }
-        int rd[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int row = row0 + i * rstep;
-          rd[i] = row < NB * NC ? rowdst[row] : 0;
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int row = row0 + i * rstep;
-          const long long o = oa + ro[i];
-          if (row < NB * NC && lane < NA)
-            cp_async<4>(A + rd[i] + lk, o >= 0 ? r + o : r, o >= 0);
+        for (int b = 0; b < NB; ++b) {
+          const long long o = oac + off[NA + b];
+          cp_async<4>(A + dac + (b >> 3) * S + (b & 7) * 4, o >= 0 ? r + o : r, o >= 0);
         }
       }
     }
@@ -376,25 +347,17 @@ fdm_kernel_tc(LevelDims dm, FdmFamily<float> fam, const float* __restrict__ r, f
          tc_pass<NA, NB, NC, 5>(A, Tb[1], mbar, phase, tmem, la, lb, lc, never, stall_ns);
     if (!ok) break;
     __syncthreads();
-    {
-      const int hw = (threadIdx.x & 31) / TcRows<NA>::W, lane = (threadIdx.x & 31) % TcRows<NA>::W;
-      const int rstep = (blockDim.x >> 5) * TcRows<NA>::R;
-      const long long oa = lane < NA ? off[lane] : 0;
-      for (int row0 = (tid >> 5) * TcRows<NA>::R + hw; row0 < NB * NC; row0 += 4 * rstep) {
-        long long ro[4];
-        float v[4];
+    // scatter: the weighted corrections (staging row b + NB c, column a) added to u,
+    // again one (a, c) line per thread walking b
+    for (int pr = tid; pr < NA * NC; pr += blockDim.x) {
+      const int a = pr % NA, c = pr / NA;
+      const long long oac = off[a] + off[NA + NB + c];
+      const float* st = A + (NB * c) * G::FS + a;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int row = row0 + i * rstep;
-          const bool in = row < NB * NC && lane < NA;
-          ro[i] = in ? rowoff[row] : kInvalidOffset;
-          v[i] = in ? A[row * G::FS + lane] : 0.0f;
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const long long o = oa + ro[i];
-          if (o >= 0) atomicAdd(u + o, v[i]);
-        }
+      for (int b = 0; b < NB; ++b) {
+        const long long o = oac + off[NA + b];
+        const float v = st[b * G::FS];
+        if (o >= 0) atomicAdd(u + o, v);
       }
     }
     __syncthreads();                             // staging, offsets and tables are rewritten next

@@ -111,6 +111,10 @@ struct FdmAxis {
   const T* W;     // [count][n*n] backward table (diag(w) S)^T, mode-major (times omega on axis 0)
   const T* lam;   // [count][n] eigenvalues in mode order
   const int* sym; // [count] 1: centro-symmetric, tables stored in even-odd folded form
+  // [count] (tcgen05 kernel; null elsewhere): the first position whose S, W and lam are
+  // identical to this one's, so that a CTA walking consecutive positions reloads tables
+  // only when they change (interior positions of a uniform axis all share one set)
+  const int* tabid;
   // Several right-hand sides stack copies of the grid along its last axis, with walls
   // between the copies: there, positions come in blocks of bpos (0: no blocks), and
   // position p starts at start0 + (p - (p / bpos) * bskip) * NP (bskip = 1 for the face

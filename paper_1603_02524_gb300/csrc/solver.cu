@@ -5,6 +5,7 @@
 // first solve of a hierarchy sequences its iterations from the host (reading the
 // residual norm once per iteration); later solves and batches replay CUDA graphs
 // whose iteration loop and convergence test run on the device.
+#include <algorithm>
 #include <array>
 #include <cmath>
 #include <cstdio>
@@ -145,6 +146,25 @@ FdmAxis<T> upload_axis(std::vector<void*>& owned, const AxisTables& t, const Axi
   ax.W = dev_upload<T>(owned, W);
   ax.lam = dev_upload<T>(owned, t.lam);
   ax.sym = dev_upload_int(owned, t.sym);
+  if (tf32) {
+    // table identity of each position: the first earlier position with the same values
+    const size_t nn = (size_t)t.n * t.n;
+    std::vector<int> id(t.count), reps;
+    for (int p = 0; p < t.count; ++p) {
+      id[p] = p;
+      for (int q : reps) {
+        if (std::equal(S.begin() + p * nn, S.begin() + (p + 1) * nn, S.begin() + q * nn) &&
+            std::equal(W.begin() + p * nn, W.begin() + (p + 1) * nn, W.begin() + q * nn) &&
+            std::equal(t.lam.begin() + (size_t)p * t.n, t.lam.begin() + (size_t)(p + 1) * t.n,
+                       t.lam.begin() + (size_t)q * t.n)) {
+          id[p] = q;
+          break;
+        }
+      }
+      if (id[p] == p) reps.push_back(p);
+    }
+    ax.tabid = dev_upload_int(owned, id);
+  }
   return ax;
 }
 
