@@ -145,6 +145,55 @@ template <typename T, int N, bool FORWARD, int SCALE = 0, typename LS = int>
 __device__ __forceinline__ void axis_pass(bool sym, T* buf, const T* M, int nlines, int lo_stride,
                                           int lo_count, int hi_stride, int stride,
                                           const T* lq = nullptr, LS lsum = LS(), int istride = 0) {
+  if constexpr (N > 32) {
+    // Long lines (P = 32 patches, 43 and 64 nodes): all N inputs in registers, the
+    // outputs in chunks of CH = 8 accumulated from 16-byte segments of the table rows (a
+    // quarter or half as many shared-memory loads as multiply-adds) and stored at once;
+    // in place, since the whole line is read first.  The vector reads stay inside a
+    // row's padding (NP_ is a multiple of the vector width).
+    using V = Vec16<T>;
+    constexpr int NP_ = padded<T>(N);
+    constexpr int CH = 8;
+    for (int l = threadIdx.x; l < nlines; l += blockDim.x) {
+      const int base = (l % lo_count) * lo_stride + (l / lo_count) * hi_stride;
+      T v[N];
+#pragma unroll
+      for (int a = 0; a < N; ++a) v[a] = buf[base + a * stride];
+      T s0 = T(0);
+      const T* tb = nullptr;
+      if constexpr (SCALE == 1) s0 = lsum(l);
+      if constexpr (SCALE == 2) tb = lq + lsum(l);
+#pragma unroll 1
+      for (int i0 = 0; i0 < N; i0 += CH) {
+        T acc[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k) acc[k] = T(0);
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+          const typename V::type* row = reinterpret_cast<const typename V::type*>(M + a * NP_ + i0);
+#pragma unroll
+          for (int c = 0; c < CH / V::W; ++c) {
+            if (i0 + c * V::W < N) {
+              const typename V::type w = row[c];
+#pragma unroll
+              for (int k = 0; k < V::W; ++k) acc[c * V::W + k] = fma(V::get(w, k), v[a], acc[c * V::W + k]);
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+          const int i = i0 + k;
+          if (i < N) {
+            T o = acc[k];
+            if constexpr (SCALE == 1) o *= recip(s0 + lq[i]);
+            if constexpr (SCALE == 2) o *= __ldg(tb + i * istride);
+            buf[base + i * stride] = o;
+          }
+        }
+      }
+    }
+    return;
+  }
   for (int l = threadIdx.x; l < nlines; l += blockDim.x) {
     const int base = (l % lo_count) * lo_stride + (l / lo_count) * hi_stride;
     T v[N], out[N];
