@@ -168,7 +168,8 @@ int pmg_grid_coords(pmg_grid g, int axis, double* out);
 int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out);
 void pmg_hierarchy_destroy(pmg_hier h);
 
-/* Number of levels L+1 and, per level, order and vector length. */
+/* Number of levels L+1 and, per level, order and vector length (nrhs vectors of
+ * the grid for a hierarchy with several right-hand sides). */
 int pmg_num_levels(pmg_hier h);
 int pmg_level_info(pmg_hier h, int level, int* P_l, long long* ndof);
 
@@ -247,7 +248,8 @@ int pmg_solve(pmg_hier h, const double* g_dev, double* u_dev, double rtol, pmg_s
 /*
  * As pmg_solve, but g_host / u_host are host arrays (pinned memory is fastest):
  * the host->device copies of g and u, the solve and the device->host copy of u
- * all run inside this call, on the hierarchy's internal device buffers.
+ * all run inside this call, on the hierarchy's internal device buffers (with
+ * nrhs > 1: nrhs vectors back to back in each array, stats as for pmg_solve).
  */
 int pmg_solve_host(pmg_hier h, const double* g_host, double* u_host, double rtol,
                    pmg_stats* stats, void* stream);
