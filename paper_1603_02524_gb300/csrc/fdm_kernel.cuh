@@ -154,6 +154,8 @@ __device__ __forceinline__ void axis_pass(bool sym, T* buf, const T* M, int nlin
     using V = Vec16<T>;
     constexpr int NP_ = padded<T>(N);
     constexpr int CH = 8;
+    constexpr int H = N / 2, NE = N - H, NO = H;
+    constexpr int PE = padded<T>(NE), PO = padded<T>(NO);
     for (int l = threadIdx.x; l < nlines; l += blockDim.x) {
       const int base = (l % lo_count) * lo_stride + (l / lo_count) * hi_stride;
       T v[N];
@@ -163,6 +165,107 @@ __device__ __forceinline__ void axis_pass(bool sym, T* buf, const T* M, int nlin
       const T* tb = nullptr;
       if constexpr (SCALE == 1) s0 = lsum(l);
       if constexpr (SCALE == 2) tb = lq + lsum(l);
+      auto put = [&](int i, T o) {
+        if constexpr (SCALE == 1) o *= recip(s0 + lq[i]);
+        if constexpr (SCALE == 2) o *= __ldg(tb + i * istride);
+        buf[base + i * stride] = o;
+      };
+      if (sym) {
+        // centro-symmetric line, tables in even-odd form (the symmetric block of NE
+        // rows, then the antisymmetric block of NO rows); halves of at most 32 values
+        const T* Me = M;
+        const T* Mo = M + NE * PE;
+        if (FORWARD) {
+          // half-sums and half-differences of the nodes, modes out symmetric first
+#pragma unroll
+          for (int a = 0; a < H; ++a) {
+            const T p = v[a] + v[N - 1 - a], m = v[a] - v[N - 1 - a];
+            v[a] = p;
+            v[N - 1 - a] = m;
+          }
+#pragma unroll 1
+          for (int i0 = 0; i0 < N; i0 += CH) {
+            // chunk of symmetric (i < NE) or antisymmetric (i >= NE) modes
+            const bool even = i0 < NE;
+            const int j0 = even ? i0 : i0 - NE;
+            T acc[CH];
+#pragma unroll
+            for (int k = 0; k < CH; ++k) acc[k] = T(0);
+            if (even) {
+#pragma unroll
+              for (int a = 0; a < NE; ++a) {
+                const typename V::type* row = reinterpret_cast<const typename V::type*>(Me + a * PE + j0);
+#pragma unroll
+                for (int c = 0; c < CH / V::W; ++c)
+                  if (j0 + c * V::W < NE) {
+                    const typename V::type w = row[c];
+#pragma unroll
+                    for (int k = 0; k < V::W; ++k) acc[c * V::W + k] = fma(V::get(w, k), v[a], acc[c * V::W + k]);
+                  }
+              }
+            } else {
+#pragma unroll
+              for (int a = 0; a < NO; ++a) {
+                const typename V::type* row = reinterpret_cast<const typename V::type*>(Mo + a * PO + j0);
+#pragma unroll
+                for (int c = 0; c < CH / V::W; ++c)
+                  if (j0 + c * V::W < NO) {
+                    const typename V::type w = row[c];
+#pragma unroll
+                    for (int k = 0; k < V::W; ++k)
+                      acc[c * V::W + k] = fma(V::get(w, k), v[N - 1 - a], acc[c * V::W + k]);
+                  }
+              }
+            }
+            const int nn = even ? NE : NO;
+#pragma unroll
+            for (int k = 0; k < CH; ++k)
+              if (j0 + k < nn) put((even ? 0 : NE) + j0 + k, acc[k]);
+            if (even && i0 + CH >= NE) i0 = NE - CH;    // the next chunk starts the odd modes
+          }
+        } else {
+          // modes in (symmetric 0..NE-1, antisymmetric NE..N-1), nodes out a and N-1-a
+#pragma unroll 1
+          for (int a0 = 0; a0 < NE; a0 += CH) {
+            T ae[CH], ao[CH];
+#pragma unroll
+            for (int k = 0; k < CH; ++k) ae[k] = ao[k] = T(0);
+#pragma unroll
+            for (int i = 0; i < NE; ++i) {
+              const typename V::type* row = reinterpret_cast<const typename V::type*>(Me + i * PE + a0);
+#pragma unroll
+              for (int c = 0; c < CH / V::W; ++c)
+                if (a0 + c * V::W < NE) {
+                  const typename V::type w = row[c];
+#pragma unroll
+                  for (int k = 0; k < V::W; ++k) ae[c * V::W + k] = fma(V::get(w, k), v[i], ae[c * V::W + k]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NO; ++i) {
+              const typename V::type* row = reinterpret_cast<const typename V::type*>(Mo + i * PO + a0);
+#pragma unroll
+              for (int c = 0; c < CH / V::W; ++c)
+                if (a0 + c * V::W < NO) {
+                  const typename V::type w = row[c];
+#pragma unroll
+                  for (int k = 0; k < V::W; ++k) ao[c * V::W + k] = fma(V::get(w, k), v[NE + i], ao[c * V::W + k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < CH; ++k) {
+              const int a = a0 + k;
+              if (a < H) {
+                put(a, ae[k] + ao[k]);
+                put(N - 1 - a, ae[k] - ao[k]);
+              } else if (a < NE) {
+                put(a, ae[k]);                       // the middle node (odd N)
+              }
+            }
+          }
+        }
+        continue;
+      }
 #pragma unroll 1
       for (int i0 = 0; i0 < N; i0 += CH) {
         T acc[CH];
@@ -181,15 +284,8 @@ __device__ __forceinline__ void axis_pass(bool sym, T* buf, const T* M, int nlin
           }
         }
 #pragma unroll
-        for (int k = 0; k < CH; ++k) {
-          const int i = i0 + k;
-          if (i < N) {
-            T o = acc[k];
-            if constexpr (SCALE == 1) o *= recip(s0 + lq[i]);
-            if constexpr (SCALE == 2) o *= __ldg(tb + i * istride);
-            buf[base + i * stride] = o;
-          }
-        }
+        for (int k = 0; k < CH; ++k)
+          if (i0 + k < N) put(i0 + k, acc[k]);
       }
     }
     return;
@@ -221,7 +317,7 @@ __device__ __forceinline__ void load_table(T* dst, const T* src, bool sym) {
   constexpr int NP_ = padded<T>(N);
   constexpr int H = N / 2, NE = N - H, NO = H;
   constexpr int PE = padded<T>(NE), PO = padded<T>(NO > 0 ? NO : 1);
-  if (sym && N > 1 && N <= 32) {
+  if (sym && N > 1 && N <= 64) {
     for (int t = threadIdx.x; t < NE * NE; t += blockDim.x) dst[(t / NE) * PE + t % NE] = src[t];
     for (int t = threadIdx.x; t < NO * NO; t += blockDim.x)
       dst[NE * PE + (t / NO) * PO + t % NO] = src[NE * NE + t];
@@ -548,7 +644,7 @@ __device__ __forceinline__ void load_table_async(T* dst, const T* src, bool sym)
   constexpr int NP_ = padded<T>(N);
   constexpr int H = N / 2, NE = N - H, NO = H;
   constexpr int PE = padded<T>(NE), PO = padded<T>(NO > 0 ? NO : 1);
-  if (sym && N > 1 && N <= 32) {
+  if (sym && N > 1 && N <= 64) {
     for (int t = threadIdx.x; t < NE * NE; t += blockDim.x)
       cp_async<sizeof(T)>(dst + (t / NE) * PE + t % NE, src + t, true);
     for (int t = threadIdx.x; t < NO * NO; t += blockDim.x)

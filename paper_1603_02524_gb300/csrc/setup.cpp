@@ -336,7 +336,7 @@ static void jacobi_or_throw(int n, std::vector<double>& A, std::vector<double>& 
 static bool centro_symmetric(const std::vector<int>& gidx, const std::vector<double>& B,
                              const std::vector<double>& Msq, const std::vector<double>& w) {
   const int n = (int)gidx.size();
-  if (n < 2 || n > 32) return false;     // the kernel folds lines of at most 32 nodes
+  if (n < 2 || n > 64) return false;     // the kernels fold lines of at most 64 nodes
   double big = 0.0;
   for (double x : B) big = std::max(big, std::fabs(x));
   for (int p = 0; p < n; ++p) {
@@ -354,7 +354,7 @@ static bool centro_symmetric(const std::vector<int>& gidx, const std::vector<dou
 // L_s S = M_s S Lambda with S^T M_s S = I, forward table S, backward table
 // W = diag(w) S stored transposed.  General form: S row-major n x n (node,
 // mode), W^T row-major (mode, node), modes by ascending lambda.
-// Centro-symmetric form (sym = 1, n <= 32): the problem splits into the
+// Centro-symmetric form (sym = 1, n <= 64): the problem splits into the
 // symmetric and antisymmetric subspaces, solved separately; S holds the
 // symmetric block (NE x NE, rows = nodes 0..NE-1) then the antisymmetric one
 // (NO x NO, rows = nodes 0..NO-1); W^T the same blocks transposed (rows =
