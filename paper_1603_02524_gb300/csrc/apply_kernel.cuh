@@ -147,29 +147,45 @@ __device__ __forceinline__ void apply_line(const ApplyTables<T>& at, const Apply
   const T* c = ax.cpl + (size_t)ax.m * (2 * PNP + 8);
   const long long estride = ax.estride;
   const int ned = ax.ned;
+  // end value and end derivative (row Drow of the differentiation matrix) of the
+  // neighbour line un.  Double-float apply of an FP64 vector: the dot product runs
+  // in FP64 and only its result and the end value are split into two fp32 words
+  // (splitting all NP values and accumulating in double-float took about half of
+  // that kernel's issue slots; the FP64 pipe is otherwise idle there)
+  auto end_terms = [&](const TIO* un, const T* Drow, const double* Drow_d, int iend, T& uend, T& dend) {
+    if constexpr (std::is_same<T, dfloat>::value && std::is_same<TIO, double>::value) {
+      double s = 0.0, v = 0.0;
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        const double val = __ldg(un + a * stride);
+        s = ::fma(__ldg(Drow_d + a), val, s);
+        if (a == iend) v = val;
+      }
+      uend = T(v);
+      dend = T(s);
+    } else {
+      T s = T(0), v = T(0);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        T val = T(__ldg(un + a * stride));
+        s = madd(ldg(Drow + a), val, s);
+        if (a == iend) v = val;
+      }
+      uend = v;
+      dend = s;
+    }
+  };
   if (ldg(c + 2 * PNP + 2) != T(0)) {          // neighbour m-1 exists
     long long en = (ax.m > 0) ? e - estride : e + (long long)(ned - 1) * estride;
-    const TIO* un = u + en * NODES + off;
-    T uP = T(0), dP = T(0);
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      T val = T(__ldg(un + a * stride));
-      dP = madd(ldg(at.DP + a), val, dP);
-      if (a == P) uP = val;
-    }
+    T uP, dP;
+    end_terms(u + en * NODES + off, at.DP, at.DPd, P, uP, dP);
     apply_axpy<T, NP>(y, c, uP);
     y[0] += ldg(c + 2 * PNP + 0) * dP - ldg(c + 2 * PNP + 1) * uP;
   }
   if (ldg(c + 2 * PNP + 5) != T(0)) {          // neighbour m+1 exists
     long long en = (ax.m < ned - 1) ? e + estride : e - (long long)(ned - 1) * estride;
-    const TIO* un = u + en * NODES + off;
-    T u0 = T(0), d0 = T(0);
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      T val = T(__ldg(un + a * stride));
-      d0 = madd(ldg(at.D0 + a), val, d0);
-      if (a == 0) u0 = val;
-    }
+    T u0, d0;
+    end_terms(u + en * NODES + off, at.D0, at.D0d, 0, u0, d0);
     apply_axpy<T, NP>(y, c + PNP, u0);
     y[P] = y[P] - (ldg(c + 2 * PNP + 3) * d0 + ldg(c + 2 * PNP + 4) * u0);
   }

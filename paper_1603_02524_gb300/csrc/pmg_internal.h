@@ -87,6 +87,8 @@ struct ApplyTables {
   const T* cpl[3];    // [Ne_d][2pad(NP)+8] neighbour coupling, scaled by M_d^-1 (see setup)
   const T* D0;        // D_{0,k}
   const T* DP;        // D_{P,k}
+  const double* D0d;  // the same rows in FP64 (the double-float apply's neighbour terms)
+  const double* DPd;
 };
 // Host-side apply tables of one axis (built from Axis1DHost by apply_axis_tables).
 struct ApplyAxisHost {

@@ -192,6 +192,8 @@ ApplyTables<T> build_apply_tables(Hier& h, int l, std::vector<void*>& own) {
   }
   at.D0 = dev_upload<T>(own, D0);
   at.DP = dev_upload<T>(own, DP);
+  at.D0d = dev_upload<double>(own, D0);
+  at.DPd = dev_upload<double>(own, DP);
   return at;
 }
 
