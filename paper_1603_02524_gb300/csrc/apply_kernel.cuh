@@ -53,6 +53,97 @@ __device__ __forceinline__ void apply_axpy(T (&acc)[N], const T* row, T x) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Transfers between orders (Sec. 3.2): J (NF x NC, J[a][o] = coarse basis function
+// o at fine GLL node a) is centro-symmetric, J[NF-1-a][NC-1-o] = J[a][o], because
+// both node sets are symmetric about the element centre.  Along one axis the
+// restriction y = J^T x and the prolongation y = J x then split into an even part
+// on the sums x[i] + x[n-1-i] and an odd part on the differences (the middle node,
+// where there is one, enters the even part alone):
+//   e[a][o] = (J[a][o] + J[a][NC-1-o]) / 2   (a <= middle, o <= middle)
+//   d[a][o] = (J[a][o] - J[a][NC-1-o]) / 2   (a, o below the middle)
+// about half the multiply-adds of the dense contraction.  The folded coefficients
+// are kernel parameters: the contractions below index them with compile-time
+// indices only, so they are read as constant operands, with no load instruction.
+// ---------------------------------------------------------------------------
+template <typename T, int NF, int NC>
+struct FoldedJ {
+  static constexpr int HF = NF / 2, HC = NC / 2, EF = NF - HF, EC = NC - HC;
+  T e[EF * EC];
+  T d[(HF * HC) > 0 ? HF * HC : 1];
+};
+template <typename T, int NF>
+struct FoldedJ<T, NF, 0> {};
+
+// host: the folded coefficients of J (row-major NF x NC, FP64), rounded to T
+template <typename T, int NF, int NC>
+FoldedJ<T, NF, NC> fold_interpolation(const double* J) {
+  using F = FoldedJ<T, NF, NC>;
+  F f{};
+  for (int a = 0; a < F::EF; ++a)
+    for (int o = 0; o < F::EC; ++o) f.e[a * F::EC + o] = T(0.5 * (J[a * NC + o] + J[a * NC + (NC - 1 - o)]));
+  for (int a = 0; a < F::HF; ++a)
+    for (int o = 0; o < F::HC; ++o) f.d[a * F::HC + o] = T(0.5 * (J[a * NC + o] - J[a * NC + (NC - 1 - o)]));
+  return f;
+}
+
+// y[0..NC) = J^T x[0..NF) along one axis; each output is handed to put(index, value)
+// as soon as it is formed (an output pair at a time), so no output array is held
+template <typename T, int NF, int NC, typename Put>
+__device__ __forceinline__ void fold_restrict(const FoldedJ<T, NF, NC>& J, const T (&x)[NF], Put&& put) {
+  using F = FoldedJ<T, NF, NC>;
+  T sp[F::EF], sm[F::HF > 0 ? F::HF : 1];
+#pragma unroll
+  for (int a = 0; a < F::HF; ++a) {
+    sp[a] = x[a] + x[NF - 1 - a];
+    sm[a] = x[a] - x[NF - 1 - a];
+  }
+  if constexpr (F::EF > F::HF) sp[F::HF] = x[F::HF];
+#pragma unroll
+  for (int o = 0; o < F::EC; ++o) {
+    T ev = T(0);
+#pragma unroll
+    for (int a = 0; a < F::EF; ++a) ev = madd(J.e[a * F::EC + o], sp[a], ev);
+    if (o < F::HC) {
+      T od = T(0);
+#pragma unroll
+      for (int a = 0; a < F::HF; ++a) od = madd(J.d[a * F::HC + o], sm[a], od);
+      put(o, ev + od);
+      put(NC - 1 - o, ev - od);
+    } else {
+      put(o, ev);
+    }
+  }
+}
+
+// y[0..NF) = J x[0..NC) along one axis, outputs handed to put(index, value)
+template <typename T, int NF, int NC, typename Put>
+__device__ __forceinline__ void fold_prolong(const FoldedJ<T, NF, NC>& J, const T (&x)[NC], Put&& put) {
+  using F = FoldedJ<T, NF, NC>;
+  T sp[F::EC], sm[F::HC > 0 ? F::HC : 1];
+#pragma unroll
+  for (int o = 0; o < F::HC; ++o) {
+    sp[o] = x[o] + x[NC - 1 - o];
+    sm[o] = x[o] - x[NC - 1 - o];
+  }
+  if constexpr (F::EC > F::HC) sp[F::HC] = x[F::HC];
+#pragma unroll
+  for (int a = 0; a < F::EF; ++a) {
+    T ev = T(0);
+#pragma unroll
+    for (int o = 0; o < F::EC; ++o) ev = madd(J.e[a * F::EC + o], sp[o], ev);
+    if (a < F::HF) {
+      T od = T(0);
+#pragma unroll
+      for (int o = 0; o < F::HC; ++o) od = madd(J.d[a * F::HC + o], sm[o], od);
+      put(a, ev + od);
+      put(NF - 1 - a, ev - od);
+    } else {
+      put(a, ev);
+    }
+  }
+}
+
 // Allow `bytes` of dynamic shared memory for kernel `fn` (once per kernel).
 template <typename K>
 static bool set_smem(K fn, size_t bytes) {
@@ -205,12 +296,12 @@ struct ApplyShape {
 
 // T: arithmetic and table type; TIO: type of u, f, v in global memory.
 // NPC > 0 (with RESIDUAL): the residual is not stored but restricted at once,
-// fc = (J (x) J (x) J)^T (f - A u) element by element (Sec. 3.2; J is NP x NPC,
-// row-major), in the operation order of the separate restriction kernel.
+// fc = (J (x) J (x) J)^T (f - A u) element by element (Sec. 3.2; J folded as in
+// FoldedJ), in the operation order of the separate restriction kernel.
 template <typename T, int DIM, int NP, bool RESIDUAL, typename TIO = T, int NPC = 0>
 __global__ void __launch_bounds__(ApplyShape<DIM, NP>::THREADS, sizeof(T) == 8 ? ApplyShape<DIM, NP>::MINB8 : 0)
 apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const TIO* __restrict__ f,
-             TIO* __restrict__ v, const T* __restrict__ J = nullptr, TIO* __restrict__ fc = nullptr) {
+             TIO* __restrict__ v, FoldedJ<T, NP, NPC> J = FoldedJ<T, NP, NPC>{}, TIO* __restrict__ fc = nullptr) {
   static_assert(NPC == 0 || (RESIDUAL && NPC < NP), "fused restriction: residual, coarser order");
   using S = ApplyShape<DIM, NP>;
   constexpr int P = NP - 1;
@@ -297,44 +388,54 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
     else v[g] = RESIDUAL ? TIO(T(f[g]) - val) : TIO(val);
   }
   if constexpr (NPC > 0) {
-    // restriction of the element residuals (in acc): x, y and z passes with J^T
+    // restriction of the element residuals (in acc): x, y and z passes with J^T,
+    // one thread per line of a pass (even-odd folded, coefficients in parameters)
     constexpr int NZF = (DIM == 3) ? NP : 1;
     constexpr int B1 = NPC * NP * NZF, B2 = NPC * NPC * NZF;
     __syncthreads();
     T* b1 = su;                                  // staged u is no longer needed
-    for (int t = tid; t < S::EPB * B1; t += blockDim.x) {
-      const int le = t / B1, tt = t - le * B1;
-      const int o = tt % NPC, rest = tt / NPC;
+    #pragma unroll 1
+    for (int t = tid; t < S::EPB * NP * NZF; t += blockDim.x) {      // x: lines (y, z)
+      const int le = t / (NP * NZF), rest = t - le * (NP * NZF);
       const T* rr = acc + le * S::NODES + rest * NP;
-      T sum = T(0);
+      T x[NP];
 #pragma unroll
-      for (int a = 0; a < NP; ++a) sum = madd(ldg(J + a * NPC + o), rr[a], sum);
-      b1[le * B1 + tt] = sum;
+      for (int a = 0; a < NP; ++a) x[a] = rr[a];
+      T* dst = b1 + le * B1 + rest * NPC;
+      fold_restrict<T, NP, NPC>(J, x, [&](int o, T v) { dst[o] = v; });
     }
     __syncthreads();
     T* b2 = acc;
-    for (int t = tid; t < S::EPB * B2; t += blockDim.x) {
-      const int le = t / B2, tt = t - le * B2;
-      const int i = tt % NPC, o = (tt / NPC) % NPC, c = tt / (NPC * NPC);
-      T sum = T(0);
+    #pragma unroll 1
+    for (int t = tid; t < S::EPB * NPC * NZF; t += blockDim.x) {     // y: lines (x', z)
+      const int le = t / (NPC * NZF), tt = t - le * (NPC * NZF);
+      const int i = tt % NPC, c = tt / NPC;
+      T x[NP];
 #pragma unroll
-      for (int a = 0; a < NP; ++a) sum = madd(ldg(J + a * NPC + o), b1[le * B1 + (c * NP + a) * NPC + i], sum);
+      for (int a = 0; a < NP; ++a) x[a] = b1[le * B1 + (c * NP + a) * NPC + i];
       if (DIM == 2) {
-        if (e0 + le < dm.nelem) fc[(e0 + le) * B2 + tt] = TIO(sum);
+        if (e0 + le < dm.nelem) {
+          TIO* dst = fc + (e0 + le) * B2 + i;
+          fold_restrict<T, NP, NPC>(J, x, [&](int o, T v) { dst[o * NPC] = TIO(v); });
+        }
       } else {
-        b2[le * B2 + tt] = sum;
+        T* dst = b2 + le * B2 + c * NPC * NPC + i;
+        fold_restrict<T, NP, NPC>(J, x, [&](int o, T v) { dst[o * NPC] = v; });
       }
     }
     if (DIM == 3) {
       __syncthreads();
       constexpr int NC3 = NPC * NPC * NPC;
-      for (int t = tid; t < S::EPB * NC3; t += blockDim.x) {
-        const int le = t / NC3, tt = t - le * NC3;
-        const int ij = tt % (NPC * NPC), o = tt / (NPC * NPC);
-        T sum = T(0);
+      #pragma unroll 1
+      for (int t = tid; t < S::EPB * NPC * NPC; t += blockDim.x) {   // z: lines (x', y')
+        const int le = t / (NPC * NPC), ij = t - le * (NPC * NPC);
+        T x[NP];
 #pragma unroll
-        for (int a = 0; a < NP; ++a) sum = madd(ldg(J + a * NPC + o), b2[le * B2 + a * NPC * NPC + ij], sum);
-        if (e0 + le < dm.nelem) fc[(e0 + le) * NC3 + tt] = TIO(sum);
+        for (int a = 0; a < NP; ++a) x[a] = b2[le * B2 + a * NPC * NPC + ij];
+        if (e0 + le < dm.nelem) {
+          TIO* dst = fc + (e0 + le) * NC3 + ij;
+          fold_restrict<T, NP, NPC>(J, x, [&](int o, T v) { dst[o * NPC * NPC] = TIO(v); });
+        }
       }
     }
   }
@@ -418,7 +519,8 @@ static int apply_dispatch(const LevelDims& dm, const ApplyTables<T>& at, const T
 // PMG_EINVAL where no fused kernel exists (the caller then runs the two kernels).
 template <typename T, int DIM, int NP, int NPC>
 static int residual_restrict_dispatch(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f,
-                                      const T* J, T* fc, cudaStream_t s) {
+                                      const double* Jh, T* fc, cudaStream_t s) {
+  const FoldedJ<T, NP, NPC> J = fold_interpolation<T, NP, NPC>(Jh);
   using S = ApplyShape<DIM, NP>;
   long long blocks = (dm.nelem + S::EPB - 1) / S::EPB;
   const size_t smem = 2 * sizeof(T) * S::EPB * S::NODES;

@@ -30,19 +30,21 @@ int launch_apply(const LevelDims& dm, const ApplyTables<T>& at, const T* u, cons
 // shapes without the fused kernel (3-D P = 32), where the caller runs the two.
 template <typename T>
 int launch_residual_restrict(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f,
-                             const T* J, T* fc, cudaStream_t s) {
+                             const T* /*J*/, const double* Jh, T* fc, cudaStream_t s) {
   if (dm.nelem == 0) return PMG_OK;
+  if (!Jh) return PMG_EINVAL;
 #define PMG_RR_CASE(DIMV, NPV, NPCV) \
-  if (dm.dim == DIMV && dm.NP == NPV) return residual_restrict_dispatch<T, DIMV, NPV, NPCV>(dm, at, u, f, J, fc, s);
+  if (dm.dim == DIMV && dm.NP == NPV) return residual_restrict_dispatch<T, DIMV, NPV, NPCV>(dm, at, u, f, Jh, fc, s);
   PMG_RR_CASE(3, 3, 2) PMG_RR_CASE(3, 5, 3) PMG_RR_CASE(3, 9, 5) PMG_RR_CASE(3, 17, 9)
   PMG_RR_CASE(2, 3, 2) PMG_RR_CASE(2, 5, 3) PMG_RR_CASE(2, 9, 5) PMG_RR_CASE(2, 17, 9) PMG_RR_CASE(2, 33, 17)
 #undef PMG_RR_CASE
   return PMG_EINVAL;
 }
 template int launch_residual_restrict<double>(const LevelDims&, const ApplyTables<double>&, const double*,
-                                              const double*, const double*, double*, cudaStream_t);
+                                              const double*, const double*, const double*, double*,
+                                              cudaStream_t);
 template int launch_residual_restrict<float>(const LevelDims&, const ApplyTables<float>&, const float*,
-                                             const float*, const float*, float*, cudaStream_t);
+                                             const float*, const float*, const double*, float*, cudaStream_t);
 
 template int launch_apply<double>(const LevelDims&, const ApplyTables<double>&, const double*,
                                   const double*, double*, cudaStream_t);
@@ -78,61 +80,63 @@ void launch_mass(const LevelDims& dm, const ApplyTables<double>& at, const doubl
 
 // ---------------------------------------------------------------------------
 // Transfers (Sec. 3.2): prolongation u_f += (J (x) J (x) J) u_c, restriction
-// f_c = (J (x) J (x) J)^T r_f, element by element.  J is NPF x NPC, row-major.
-// One CTA per element; three passes through shared memory.
+// f_c = (J (x) J (x) J)^T r_f, element by element, with J even-odd folded (FoldedJ
+// in apply_kernel.cuh).  One CTA per element; three passes through shared memory,
+// one thread per line of a pass.
 // ---------------------------------------------------------------------------
 template <typename T, int DIM, int NPF, int NPC, bool PROLONG>
 __global__ void __launch_bounds__(256)
-transfer_kernel(long long nelem, const T* __restrict__ J, const T* __restrict__ in,
-                T* __restrict__ out) {
+transfer_kernel(long long nelem, FoldedJ<T, NPF, NPC> J, const T* __restrict__ in, T* __restrict__ out) {
   constexpr int NIN = PROLONG ? NPC : NPF;      // per-axis size of the input
   constexpr int NOUT = PROLONG ? NPF : NPC;
   constexpr int NZI = (DIM == 3) ? NIN : 1;
   constexpr int NZO = (DIM == 3) ? NOUT : 1;
   extern __shared__ __align__(16) unsigned char tr_smem[];
-  T* sJ = reinterpret_cast<T*>(tr_smem);
-  T* b0 = sJ + NPF * NPC;
+  T* b0 = reinterpret_cast<T*>(tr_smem);
   T* b1 = b0 + NIN * NIN * NZI;
   T* b2 = b1 + NOUT * NIN * NZI;
   const long long e = blockIdx.x;
-  for (int t = threadIdx.x; t < NPF * NPC; t += blockDim.x) sJ[t] = J[t];
   for (int t = threadIdx.x; t < NIN * NIN * NZI; t += blockDim.x)
     b0[t] = in[e * (NIN * NIN * NZI) + t];
   __syncthreads();
-  // matrix entry mapping input index a -> output index o along one axis
-  auto Jm = [&](int o, int a) { return PROLONG ? sJ[o * NPC + a] : sJ[a * NPC + o]; };
-  for (int t = threadIdx.x; t < NOUT * NIN * NZI; t += blockDim.x) {   // x pass
-    int o = t % NOUT, rest = t / NOUT;
-    T s = 0;
+  // one axis line: NIN inputs `sstride` apart -> NOUT outputs (even-odd folded J),
+  // each handed to put(index, value)
+  auto line = [&](const T* src, int sstride, auto&& put) {
+    T x[NIN];
 #pragma unroll
-    for (int a = 0; a < NIN; ++a) s = fma(Jm(o, a), b0[rest * NIN + a], s);
-    b1[t] = s;
+    for (int a = 0; a < NIN; ++a) x[a] = src[a * sstride];
+    if constexpr (PROLONG) fold_prolong<T, NPF, NPC>(J, x, put);
+    else fold_restrict<T, NPF, NPC>(J, x, put);
+  };
+#pragma unroll 1
+  for (int r = threadIdx.x; r < NIN * NZI; r += blockDim.x) {          // x: lines (y, z)
+    T* dst = b1 + r * NOUT;
+    line(b0 + r * NIN, 1, [&](int o, T v) { dst[o] = v; });
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < NOUT * NOUT * NZI; t += blockDim.x) {  // y pass
-    int i = t % NOUT, o = (t / NOUT) % NOUT, c = t / (NOUT * NOUT);
-    T s = 0;
-#pragma unroll
-    for (int a = 0; a < NIN; ++a) s = fma(Jm(o, a), b1[(c * NIN + a) * NOUT + i], s);
-    b2[t] = s;
-  }
-  __syncthreads();
-  if (DIM == 2) {
-    for (int t = threadIdx.x; t < NOUT * NOUT; t += blockDim.x) {
-      long long g = e * (NOUT * NOUT) + t;
-      if (PROLONG) out[g] += b2[t];
-      else out[g] = b2[t];
+#pragma unroll 1
+  for (int t = threadIdx.x; t < NOUT * NZI; t += blockDim.x) {         // y: lines (x', z)
+    const int i = t % NOUT, c = t / NOUT;
+    if (DIM == 2) {
+      T* dst = out + e * (NOUT * NOUT) + i;
+      line(b1 + c * NIN * NOUT + i, NOUT, [&](int o, T v) {
+        if (PROLONG) dst[o * NOUT] += v;
+        else dst[o * NOUT] = v;
+      });
+    } else {
+      T* dst = b2 + c * NOUT * NOUT + i;
+      line(b1 + c * NIN * NOUT + i, NOUT, [&](int o, T v) { dst[o * NOUT] = v; });
     }
-    return;
   }
-  for (int t = threadIdx.x; t < NOUT * NOUT * NZO; t += blockDim.x) {  // z pass
-    int ij = t % (NOUT * NOUT), o = t / (NOUT * NOUT);
-    T s = 0;
-#pragma unroll
-    for (int a = 0; a < NIN; ++a) s = fma(Jm(o, a), b2[a * NOUT * NOUT + ij], s);
-    long long g = e * (NOUT * NOUT * NZO) + t;
-    if (PROLONG) out[g] += s;
-    else out[g] = s;
+  if (DIM == 2) return;
+  __syncthreads();
+#pragma unroll 1
+  for (int ij = threadIdx.x; ij < NOUT * NOUT; ij += blockDim.x) {     // z: lines (x', y')
+    T* dst = out + e * (NOUT * NOUT * NZO) + ij;
+    line(b2 + ij, NOUT * NOUT, [&](int o, T v) {
+      if (PROLONG) dst[o * NOUT * NOUT] += v;
+      else dst[o * NOUT * NOUT] = v;
+    });
   }
 }
 
@@ -220,17 +224,20 @@ transfer_big_kernel(long long nelem, const T* __restrict__ J, const T* __restric
 }
 
 template <typename T, bool PROLONG>
-static int transfer_launch(const LevelDims& fine, const LevelDims& coarse, const T* J, const T* in,
-                           T* out, cudaStream_t s) {
+static int transfer_launch(const LevelDims& fine, const LevelDims& coarse, const T* J, const double* Jh,
+                           const T* in, T* out, cudaStream_t s) {
   if (fine.nelem == 0) return PMG_OK;
   unsigned blocks = (unsigned)fine.nelem;
 #define PMG_TR_CASE(DIMV, NPF, NPC) \
   if (fine.dim == DIMV && fine.NP == NPF && coarse.NP == NPC) { \
+    if (!Jh) return PMG_EINVAL; \
     constexpr int NIN = PROLONG ? NPC : NPF, NOUT = PROLONG ? NPF : NPC; \
     constexpr int NZI = DIMV == 3 ? NIN : 1; \
-    const size_t smem = sizeof(T) * (NPF * NPC + NIN * NIN * NZI + NOUT * NIN * NZI + NOUT * NOUT * NZI); \
+    const size_t smem = sizeof(T) * (NIN * NIN * NZI + NOUT * NIN * NZI + NOUT * NOUT * NZI); \
     if (!set_smem(transfer_kernel<T, DIMV, NPF, NPC, PROLONG>, smem)) return PMG_ECUDA; \
-    count_launch(); transfer_kernel<T, DIMV, NPF, NPC, PROLONG><<<blocks, 256, smem, s>>>(fine.nelem, J, in, out); \
+    count_launch(); \
+    transfer_kernel<T, DIMV, NPF, NPC, PROLONG><<<blocks, 256, smem, s>>>( \
+        fine.nelem, fold_interpolation<T, NPF, NPC>(Jh), in, out); \
     return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA; }
   PMG_TR_CASE(3, 3, 2) PMG_TR_CASE(3, 5, 3) PMG_TR_CASE(3, 9, 5) PMG_TR_CASE(3, 17, 9)
   PMG_TR_CASE(2, 3, 2) PMG_TR_CASE(2, 5, 3) PMG_TR_CASE(2, 9, 5) PMG_TR_CASE(2, 17, 9)
@@ -246,23 +253,23 @@ static int transfer_launch(const LevelDims& fine, const LevelDims& coarse, const
 }
 
 template <typename T>
-int launch_restrict(const LevelDims& fine, const LevelDims& coarse, const T* J, const T* rf, T* fc,
-                    cudaStream_t s) {
-  return transfer_launch<T, false>(fine, coarse, J, rf, fc, s);
+int launch_restrict(const LevelDims& fine, const LevelDims& coarse, const T* J, const double* Jh,
+                    const T* rf, T* fc, cudaStream_t s) {
+  return transfer_launch<T, false>(fine, coarse, J, Jh, rf, fc, s);
 }
 template <typename T>
-int launch_prolong(const LevelDims& fine, const LevelDims& coarse, const T* J, const T* uc, T* uf,
-                   cudaStream_t s) {
-  return transfer_launch<T, true>(fine, coarse, J, uc, uf, s);
+int launch_prolong(const LevelDims& fine, const LevelDims& coarse, const T* J, const double* Jh,
+                   const T* uc, T* uf, cudaStream_t s) {
+  return transfer_launch<T, true>(fine, coarse, J, Jh, uc, uf, s);
 }
-template int launch_restrict<double>(const LevelDims&, const LevelDims&, const double*,
+template int launch_restrict<double>(const LevelDims&, const LevelDims&, const double*, const double*,
                                      const double*, double*, cudaStream_t);
-template int launch_restrict<float>(const LevelDims&, const LevelDims&, const float*, const float*,
-                                    float*, cudaStream_t);
-template int launch_prolong<double>(const LevelDims&, const LevelDims&, const double*,
+template int launch_restrict<float>(const LevelDims&, const LevelDims&, const float*, const double*,
+                                    const float*, float*, cudaStream_t);
+template int launch_prolong<double>(const LevelDims&, const LevelDims&, const double*, const double*,
                                     const double*, double*, cudaStream_t);
-template int launch_prolong<float>(const LevelDims&, const LevelDims&, const float*, const float*,
-                                   float*, cudaStream_t);
+template int launch_prolong<float>(const LevelDims&, const LevelDims&, const float*, const double*,
+                                   const float*, float*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Exact coarse solve at P = 1 (A_0^+ f_0): the coarse operator is

@@ -225,9 +225,11 @@ struct Hier {
   LevelDev<double> d64[kMaxLevels];
   LevelDev<float> d32[kMaxLevels];
   bool has32 = false;
-  // interpolation J_l (fine NP x coarse NP), l = 1..L
+  // interpolation J_l (fine NP x coarse NP), l = 1..L; the host copy feeds the
+  // even-odd folded coefficients that the transfer kernels take as parameters
   double* J64[kMaxLevels] = {};
   float* J32[kMaxLevels] = {};
+  std::vector<double> Jhost[kMaxLevels];
   CoarseFdm coarse{};
   // host copies of the patch-table shapes and symmetry flags (S/W/lam cleared)
   std::vector<AxisTables> ec_shape[kMaxLevels], fc_shape[kMaxLevels];
@@ -309,17 +311,20 @@ void stack_tables(const AxisTables& t, int k, int skip, AxisTables& out);
 template <typename T>
 int launch_apply(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f, T* v,
                  cudaStream_t s);
+// Transfers: J the device copy of J_l (used where the kernels contract densely,
+// 3-D P = 32 <-> 16), Jh the host copy (fine x coarse, row-major), folded into the
+// kernel parameters of the others.
 template <typename T>
 int launch_residual_restrict(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f,
-                             const T* J, T* fc, cudaStream_t s);
+                             const T* J, const double* Jh, T* fc, cudaStream_t s);
 template <typename T>
 int launch_fdm(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, cudaStream_t s);
 template <typename T>
-int launch_restrict(const LevelDims& fine, const LevelDims& coarse, const T* J, const T* rf, T* fc,
-                    cudaStream_t s);
+int launch_restrict(const LevelDims& fine, const LevelDims& coarse, const T* J, const double* Jh,
+                    const T* rf, T* fc, cudaStream_t s);
 template <typename T>
-int launch_prolong(const LevelDims& fine, const LevelDims& coarse, const T* J, const T* uc, T* uf,
-                   cudaStream_t s);
+int launch_prolong(const LevelDims& fine, const LevelDims& coarse, const T* J, const double* Jh,
+                   const T* uc, T* uf, cudaStream_t s);
 int launch_apply_df(const LevelDims& dm, const ApplyTables<dfloat>& at, const double* u,
                     const double* f, double* v, cudaStream_t s);
 int launch_coarse_fdm(const LevelDims& dm, const CoarseFdm& c, const double* f, double* u,

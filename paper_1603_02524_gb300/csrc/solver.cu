@@ -410,10 +410,11 @@ void vcycle(Hier& h, const T* fL, T* uL, cudaStream_t s) {
     T* J = nullptr;
     if constexpr (sizeof(T) == 8) J = (T*)h.J64[l]; else J = (T*)h.J32[l];
     // f_{l-1} = I^T (f_l - A u_l): one fused kernel, else residual and restriction apart
-    const int rr = launch_residual_restrict<T>(h.dims[l], d.at, u[l], f[l], J, lev<T>(h, l - 1).f, s);
+    const int rr = launch_residual_restrict<T>(h.dims[l], d.at, u[l], f[l], J, h.Jhost[l].data(),
+                                               lev<T>(h, l - 1).f, s);
     if (rr == PMG_EINVAL) {
       PMG_CHECK(launch_apply<T>(h.dims[l], d.at, u[l], f[l], d.r, s));
-      PMG_CHECK(launch_restrict<T>(h.dims[l], h.dims[l - 1], J, d.r, lev<T>(h, l - 1).f, s));
+      PMG_CHECK(launch_restrict<T>(h.dims[l], h.dims[l - 1], J, h.Jhost[l].data(), d.r, lev<T>(h, l - 1).f, s));
     } else {
       PMG_CHECK(rr);
     }
@@ -429,7 +430,7 @@ void vcycle(Hier& h, const T* fL, T* uL, cudaStream_t s) {
   for (int l = 1; l <= L; ++l) {
     T* J = nullptr;
     if constexpr (sizeof(T) == 8) J = (T*)h.J64[l]; else J = (T*)h.J32[l];
-    PMG_CHECK(launch_prolong<T>(h.dims[l], h.dims[l - 1], J, u[l - 1], u[l], s));
+    PMG_CHECK(launch_prolong<T>(h.dims[l], h.dims[l - 1], J, h.Jhost[l].data(), u[l - 1], u[l], s));
     smooth_level<T>(h, l, u[l], f[l], ns_level(h, l, true), false, s);
   }
 }
@@ -1009,6 +1010,7 @@ int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
         lagrange_matrix(h->axes[l - 1][0].eta, h->axes[l][0].eta, J);
         h->J64[l] = dev_upload<double>(h->owned, J);
         h->J32[l] = dev_upload<float>(h->owned, J);
+        h->Jhost[l] = J;
       }
     }
     h->has32 = o.precision != PMG_PREC_FP64;
@@ -1141,8 +1143,8 @@ int pmg_restrict(pmg_hier hh, int level, const double* rf, double* fc, void* str
   Hier* h = H(hh);
   if (!h || level < 1 || level > h->L || !rf || !fc) return PMG_EINVAL;
   return guarded(h, [&] {
-    return launch_restrict<double>(h->dims[level], h->dims[level - 1], h->J64[level], rf, fc,
-                                   (cudaStream_t)stream);
+    return launch_restrict<double>(h->dims[level], h->dims[level - 1], h->J64[level], h->Jhost[level].data(),
+                                   rf, fc, (cudaStream_t)stream);
   });
 }
 
@@ -1150,8 +1152,8 @@ int pmg_prolong(pmg_hier hh, int level, const double* uc, double* uf, void* stre
   Hier* h = H(hh);
   if (!h || level < 1 || level > h->L || !uc || !uf) return PMG_EINVAL;
   return guarded(h, [&] {
-    return launch_prolong<double>(h->dims[level], h->dims[level - 1], h->J64[level], uc, uf,
-                                  (cudaStream_t)stream);
+    return launch_prolong<double>(h->dims[level], h->dims[level - 1], h->J64[level], h->Jhost[level].data(),
+                                  uc, uf, (cudaStream_t)stream);
   });
 }
 
