@@ -62,6 +62,15 @@ TRAFFIC_PER_PATCH = {
     ("double", 16, "EA", 3): (325.70e6 + 118.69e6) / 4096,   # fdm_kernel<double,23,23,23>, 16^3 elements
 }
 
+# Shared-memory data-pipe wavefronts per patch of the tcgen05 patch kernel (load/store
+# unit + tensor-core operand reads), from its ncu capture (profiles/
+# fdm_kernel_tc_23_poisson3d_16cube_P16.md, 4096 patches of 23^3): the pipe this kernel
+# is bound by.  Key: (P, family).  Utilisation = wavefronts / (SMs x SM clock x sweep
+# time) at one wavefront per SM and cycle.
+TC_SMEM_WAVEFRONTS_PER_PATCH = {
+    (16, "EA"): (38481661 + 14745600) / 4096,
+}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -701,12 +710,24 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
         pk_o = peaks["fp64" if prec == "fp64" else "fp32"] / 1e3
         if prec == "mixed_tf32" and w.dim == 3 and w.P >= 8:   # tcgen05 patch kernel: tf32 tensor peak
             pk_o = TF32_PEAK_GFLOPS / 1e3
+        smem_frac = None
+        if prec == "mixed_tf32" and w.dim == 3 and (w.P, "EA" if fam == -1 else "FA") in TC_SMEM_WAVEFRONTS_PER_PATCH:
+            wf = TC_SMEM_WAVEFRONTS_PER_PATCH[(w.P, "EA" if fam == -1 else "FA")] * nelem
+            mhz = (line.get("clocks") or {}).get("sm_mhz") or (line.get("clocks") or {}).get("sm_max_mhz")
+            nsm = torch.cuda.get_device_properties(local).multi_processor_count
+            if mhz:
+                smem_frac = wf / (nsm * mhz * 1e6 * ms_o * 1e-3)
         entry = {"value": n / (t_o * 1e-3), "unit": "DOF/s", "ms_per_step": t_o, "iterations": itm,
                  "status": rc, "max_rel_diff_between_solutions": rel, "patch_sweep_ms": ms_o,
                  "smoother_gdof_s": n / (ms_o * 1e-3) / 1e9,
                  "smoother_roofline_frac": fl_o / (ms_o * 1e-3) / 1e12 / pk_o,
                  "smoother_peak": ("TF32 tensor (measured bf16 x 1/2)" if pk_o * 1e3 == TF32_PEAK_GFLOPS
                                    else f"{'FP64' if prec == 'fp64' else 'FP32'} FMA, measured")}
+        if smem_frac is not None:
+            entry["smoother_smem_pipe_frac"] = smem_frac
+            entry["smoother_smem_pipe_note"] = ("shared-memory data-pipe wavefronts per patch from the ncu "
+                                                "capture x patches / (SMs x SM clock x sweep time); the bound "
+                                                "of the tcgen05 patch kernel")
         if other == "fp64_plain":
             line["fp64_plain"] = entry
             line["speedup_vs_fp64"] = t_o / line["ms_per_step"]
