@@ -743,9 +743,13 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
         t0 = time.perf_counter()
         net, hist, _ = learned.train_default()
         t_train = time.perf_counter() - t0
-        om, ta = net.level_params(w.P, w.spacing)
+        # the network's parameters, judged on this grid by the measured MGCG rate with the
+        # paper's omega = tau = 1 as fallback
+        om, ta, kept, rate_l, rate_p = learned.judged_params(net, w.P, w.n_elem, w.spacing,
+                                                             opts["smoother"], opts.get("variable_v", False))
+        om_net, ta_net = net.level_params(w.P, w.spacing)
         hl = Hierarchy(grid, precision=args.precision, outer_apply=args.outer_apply, omega_level=om,
-                       tau_level=ta, **opts)
+                       tau_level=ta, **opts)       # None, None: the paper's values (fallback)
         if args.autotune:
             hl.autotune()
         ul = torch.zeros_like(g)
@@ -765,7 +769,9 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
                            "ms_per_step": statistics.mean(tl), "iterations": itl, "status": rcl,
                            "paper_parameters_iterations": line["config"]["iterations"],
                            "speedup_vs_paper_parameters": line["ms_per_step"] / statistics.mean(tl),
-                           "omega_level": om[1:], "tau_level": ta[1:], "training_s": t_train,
+                           "omega_level": om_net[1:], "tau_level": ta_net[1:], "training_s": t_train,
+                           "judged_rates": {"learned": rate_l, "paper": rate_p,
+                                            "kept_learned": kept},
                            "training_loss": [hist[0], hist[-1]]}
         hl.close()
     # --- FP64 CPU oracle on this host (bounded sample)

@@ -194,10 +194,17 @@ class GridConfig:
 
 def measure_rate(cfg: GridConfig, omega_level=None, tau_level=None, iters=8, seed=0):
     """MGCG residual-reduction rate rho = (r_n / r_0)^(1/n) on a seeded random RHS."""
+    return measure_rate_grid(cfg.P, cfg.n_elem, cfg.spacing(), cfg.smoother, cfg.variable_v, omega_level,
+                             tau_level, iters=iters, seed=seed, periodic=cfg.periodic)
+
+
+def measure_rate_grid(P, n_elem, spacing, smoother="FA", variable_v=True, omega_level=None, tau_level=None,
+                      iters=8, seed=0, periodic=False):
+    """measure_rate on a grid given by its per-axis element widths."""
     import torch
-    g = Grid(3, cfg.P, cfg.n_elem, cfg.spacing(), periodic=cfg.periodic)
-    h = Hierarchy(g, smoother=cfg.smoother, overlap="l", max_iter=iters, omega_level=omega_level,
-                  tau_level=tau_level, variable_v=cfg.variable_v)
+    g = Grid(3, P, tuple(n_elem), spacing, periodic=periodic)
+    h = Hierarchy(g, smoother=smoother, overlap="l", max_iter=iters, omega_level=omega_level,
+                  tau_level=tau_level, variable_v=variable_v)
     n = h.ndof()
     gen = torch.Generator(device="cuda").manual_seed(seed)
     f = torch.rand(n, dtype=torch.float64, device="cuda", generator=gen) * 2 - 1
@@ -210,6 +217,20 @@ def measure_rate(cfg: GridConfig, omega_level=None, tau_level=None, iters=8, see
     hist = [x for x in hist if x > 0]
     k = len(hist) - 1
     return (hist[-1] / hist[0]) ** (1.0 / k) if k > 0 else 0.0
+
+
+def judged_params(net, P, n_elem, spacing, smoother="FA", variable_v=True, iters=8):
+    """The network's per-level (omega, tau) for a grid, judged by the measured convergence
+    rate: kept only if an MGCG run of `iters` iterations on this grid converges at least as
+    fast as with the paper's omega = tau = 1, else the paper's values (the fallback).
+    Returns (omega_level, tau_level, kept, rate_learned, rate_paper); omega_level and
+    tau_level are None for the fallback."""
+    om, ta = net.level_params(P, spacing)
+    learned_rate = measure_rate_grid(P, n_elem, spacing, smoother, variable_v, om, ta, iters=iters)
+    paper_rate = measure_rate_grid(P, n_elem, spacing, smoother, variable_v, None, None, iters=iters)
+    if learned_rate <= paper_rate:
+        return om, ta, True, learned_rate, paper_rate
+    return None, None, False, learned_rate, paper_rate
 
 
 # Candidate (omega, tau) pairs.  Measured on 4^3-element grids, P = 2..8: the paper's
