@@ -875,6 +875,143 @@ fdm_kernel_gbuf(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __re
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same large patches in slabs: the forward passes along a and b act within each
+// c-plane, so they run in shared memory a few planes (a slab of CS) at a time; the
+// planes go to the CTA's scratch buffer, the c-lines are transformed there (forward
+// with the eigenvalue scaling, then backward), and the backward b and a passes run
+// slab by slab in shared memory again before the weighted scatter.  The scratch
+// buffer is written once and read once around the c passes instead of around all
+// six passes.  Plane rows are padded to NA + 1 values (odd), so that the a-lines of
+// consecutive threads fall into distinct shared-memory banks.
+// ---------------------------------------------------------------------------
+template <typename T, int NA, int NB, int NC>
+struct SlabShape {
+  static constexpr int NAP = NA % 2 == 0 ? NA + 1 : NA;  // odd row stride
+  static constexpr int MAXT = sizeof(T) == 8 ? 256 : 512;  // long lines in registers: 255 / 128 per thread
+  static constexpr int PL = NB * NAP;                       // floats of one padded plane
+  static constexpr size_t FIXED = sizeof(long long) * ((NA + NB + NC + 1) / 2 * 2 + (NB * NC + 1) / 2 * 2) +
+                                  sizeof(T) * (2 * (size_t)(table_floats<T, false>(NA) + table_floats<T, false>(NB) +
+                                                            table_floats<T, false>(NC)) + NA + NB + NC);
+  static constexpr size_t BUDGET = 227 * 1024;
+  static constexpr int CS_FIT = FIXED < BUDGET ? (int)((BUDGET - FIXED) / (sizeof(T) * PL)) : 0;
+  static constexpr int CS = CS_FIT > 8 ? 8 : CS_FIT;       // planes per slab
+  static constexpr size_t BYTES = FIXED + sizeof(T) * (size_t)CS * PL;
+};
+
+template <typename T, int NA, int NB, int NC>
+__global__ void __launch_bounds__(SlabShape<T, NA, NB, NC>::MAXT)
+fdm_kernel_slab(LevelDims dm, FdmFamily<T> fam, const T* __restrict__ r, T* __restrict__ u) {
+  using SS = SlabShape<T, NA, NB, NC>;
+  constexpr int NAP = SS::NAP, CS = SS::CS, PL = SS::PL;
+  extern __shared__ __align__(16) unsigned char fdm_smem[];
+  long long* off = reinterpret_cast<long long*>(fdm_smem);
+  long long* rowoff = off + (NA + NB + NC + 1) / 2 * 2;
+  T* tb = reinterpret_cast<T*>(rowoff + (NB * NC + 1) / 2 * 2);
+  T* const Sq[3] = {tb, tb + 2 * table_floats<T, false>(NA),
+                    tb + 2 * (table_floats<T, false>(NA) + table_floats<T, false>(NB))};
+  T* const Wq[3] = {Sq[0] + table_floats<T, false>(NA), Sq[1] + table_floats<T, false>(NB),
+                    Sq[2] + table_floats<T, false>(NC)};
+  T* la = Sq[2] + 2 * table_floats<T, false>(NC);
+  T* lb = la + NA;
+  T* lc = lb + NB;
+  T* sb = lc + NC;                                          // CS padded planes [k][b][a]
+  T* buf = fam.scratch + (long long)blockIdx.x * fam.scratch_stride;   // [c][b][a]
+  const int ca = fam.ax[0].count, cb = fam.ax[1].count;
+  const int nq[3] = {NA, NB, NC};
+  T* lq[3] = {la, lb, lc};
+  long long* offq[3] = {off, off + NA, off + NA + NB};
+  const long long nodes_el = (long long)dm.NP * dm.NP * dm.NPz;
+  const long long estride[3] = {nodes_el, nodes_el * dm.ne[0], nodes_el * dm.ne[0] * dm.ne[1]};
+  const long long nstride[3] = {1, dm.NP, (long long)dm.NP * dm.NP};
+  for (int pid = blockIdx.x; pid < fam.count_total; pid += gridDim.x) {
+    const int pidx[3] = {pid % ca, (pid / ca) % cb, pid / (ca * cb)};
+    bool sym[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const FdmAxis<T>& ax = fam.ax[q];
+      const int n = nq[q];
+      const size_t p = pidx[q];
+      sym[q] = ax.sym[p] != 0;
+      if (q == 0) {
+        load_table<T, NA>(Sq[0], ax.S + p * n * n, sym[0]);
+        load_table<T, NA>(Wq[0], ax.W + p * n * n, sym[0]);
+      } else if (q == 1) {
+        load_table<T, NB>(Sq[1], ax.S + p * n * n, sym[1]);
+        load_table<T, NB>(Wq[1], ax.W + p * n * n, sym[1]);
+      } else {
+        load_table<T, NC>(Sq[2], ax.S + p * n * n, sym[2]);
+        load_table<T, NC>(Wq[2], ax.W + p * n * n, sym[2]);
+      }
+      for (int a = threadIdx.x; a < n; a += blockDim.x) {
+        lq[q][a] = ax.lam[p * n + a];
+        const int ph = ax.phys;
+        const int npp = (ph == 2) ? dm.NPz : dm.NP;
+        int G = patch_start(ax, (int)p, npp) + a;
+        long long o;
+        if (ax.periodic) {
+          G %= ax.N;
+          if (G < 0) G += ax.N;
+          o = (long long)(G / npp) * estride[ph] + (G % npp) * nstride[ph];
+        } else if (G < 0 || G >= ax.N) {
+          o = kInvalidOffset;
+        } else {
+          o = (long long)(G / npp) * estride[ph] + (G % npp) * nstride[ph];
+        }
+        offq[q][a] = o;
+      }
+    }
+    __syncthreads();
+    for (int rr = threadIdx.x; rr < NB * NC; rr += blockDim.x)
+      rowoff[rr] = off[NA + rr % NB] + off[NA + NB + rr / NB];
+    __syncthreads();
+    // forward a and b, slab by slab
+    for (int c0 = 0; c0 < NC; c0 += CS) {
+      const int cs = NC - c0 < CS ? NC - c0 : CS;
+      for (int t = threadIdx.x; t < cs * NB * NA; t += blockDim.x) {
+        const int row = t / NA, a = t - row * NA;              // row = b + NB k
+        const long long o = off[a] + rowoff[c0 * NB + row];
+        sb[row * NAP + a] = o >= 0 ? r[o] : T(0);
+      }
+      __syncthreads();
+      axis_pass<T, NA, true>(sym[0], sb, Sq[0], NB * cs, NAP, NB * cs, 0, 1);
+      __syncthreads();
+      axis_pass<T, NB, true>(sym[1], sb, Sq[1], NA * cs, 1, NA, PL, NAP);
+      __syncthreads();
+      for (int t = threadIdx.x; t < cs * NB * NA; t += blockDim.x) {
+        const int row = t / NA, a = t - row * NA;
+        buf[(long long)c0 * NB * NA + t] = sb[row * NAP + a];
+      }
+      __syncthreads();
+    }
+    // c: forward with the scaling by 1 / (lambda_a + lambda_b + lambda_c), backward
+    axis_pass<T, NC, true, 1>(sym[2], buf, Sq[2], NA * NB, 1, NA * NB, 0, NA * NB, lc,
+                              [&](int l) { return la[l % NA] + lb[l / NA]; });
+    __syncthreads();
+    axis_pass<T, NC, false>(sym[2], buf, Wq[2], NA * NB, 1, NA * NB, 0, NA * NB);
+    __syncthreads();
+    // backward b and a, slab by slab, and the weighted corrections added to u
+    for (int c0 = 0; c0 < NC; c0 += CS) {
+      const int cs = NC - c0 < CS ? NC - c0 : CS;
+      for (int t = threadIdx.x; t < cs * NB * NA; t += blockDim.x) {
+        const int row = t / NA, a = t - row * NA;
+        sb[row * NAP + a] = buf[(long long)c0 * NB * NA + t];
+      }
+      __syncthreads();
+      axis_pass<T, NB, false>(sym[1], sb, Wq[1], NA * cs, 1, NA, PL, NAP);
+      __syncthreads();
+      axis_pass<T, NA, false>(sym[0], sb, Wq[0], NB * cs, NAP, NB * cs, 0, 1);
+      __syncthreads();
+      for (int t = threadIdx.x; t < cs * NB * NA; t += blockDim.x) {
+        const int row = t / NA, a = t - row * NA;
+        const long long o = off[a] + rowoff[c0 * NB + row];
+        if (o >= 0) atomicAdd(u + o, sb[row * NAP + a]);
+      }
+      __syncthreads();
+    }
+  }
+}
+
 template <typename T, int NA, int NB, int NC, bool TC>
 constexpr size_t fdm_smem_bytes() {
   return sizeof(long long) * ((NA + NB + NC + 1) / 2 * 2 + (NB * NC + 1) / 2 * 2) +
@@ -938,9 +1075,27 @@ int fdm_launch(const LevelDims& dm, const FdmFamily<T>& fam, const T* r, T* u, c
                              (int)smem_g) != cudaSuccess)
       return PMG_ECUDA;
     if (fam.count_total <= 0) return PMG_OK;
+    const int grid = fam.count_total < fam.scratch_ctas ? fam.count_total : fam.scratch_ctas;
+    using SS = SlabShape<T, NA, NB, NC>;
+    // slab form (3-D) or scratch form: the tuner times both (variant 1 / 0); untuned,
+    // the slab form for fp32 face patches (FA P = 32: 13.8 -> 11.1 ms per family sweep
+    // of 8^3 elements with four right-hand sides), the scratch form otherwise (fp32 EA
+    // 4.3 against 4.9 ms, FP64 FA 110 against 123 ms)
+    const bool slab = fam.variant < 0 ? (sizeof(T) == 4 && NA != NB) : fam.variant == 1;
+    if constexpr (NC > 1 && SS::CS >= 1) if (slab) {
+      // CTA size from the tuner, up to SS::MAXT
+      if (SS::BYTES > 48 * 1024 &&
+          cudaFuncSetAttribute(fdm_kernel_slab<T, NA, NB, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)SS::BYTES) != cudaSuccess)
+        return PMG_ECUDA;
+      int threads = (fam.threads >= 32 && fam.threads % 32 == 0) ? fam.threads : SS::MAXT;
+      if (threads > SS::MAXT) threads = SS::MAXT;
+      count_launch();
+      fdm_kernel_slab<T, NA, NB, NC><<<grid, threads, SS::BYTES, s>>>(dm, fam, r, u);
+      return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
+    }
     int threads = (fam.threads >= 32 && fam.threads % 32 == 0) ? fam.threads : 256;
     if (threads > 256) threads = 256;
-    const int grid = fam.count_total < fam.scratch_ctas ? fam.count_total : fam.scratch_ctas;
     count_launch();
     fdm_kernel_gbuf<T, NA, NB, NC><<<grid, threads, smem_g, s>>>(dm, fam, r, u);
     return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;

@@ -708,8 +708,9 @@ int tune_family(Hier& h, int l, FdmFamily<T>& fam, LevelDev<T>& d, cudaStream_t 
   PMG_CUDA(cudaEventCreate(&e1));
   int best = 0, best_v = -1;
   float best_ms = 1e30f;
-  // fp32 families: both kernel forms (one patch per CTA, pipelined persistent CTAs)
-  const int nvar = sizeof(T) == 4 && !fam.tc ? 2 : 1;
+  // fp32 families: both kernel forms (one patch per CTA, pipelined persistent CTAs);
+  // patches too large for shared memory (a scratch buffer attached): scratch or slab form
+  const int nvar = (sizeof(T) == 4 && !fam.tc) || fam.scratch ? 2 : 1;
   try {
     for (int v = 0; v < nvar; ++v) {
       for (int ci = 0; ci < ncand; ++ci) {
