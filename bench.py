@@ -714,7 +714,7 @@ def extras(args, w, opts, grid, h, g, u, dev, stream, line, lib):
         if prec == "mixed_tf32" and w.dim == 3 and (w.P, "EA" if fam == -1 else "FA") in TC_SMEM_WAVEFRONTS_PER_PATCH:
             wf = TC_SMEM_WAVEFRONTS_PER_PATCH[(w.P, "EA" if fam == -1 else "FA")] * nelem
             mhz = (line.get("clocks") or {}).get("sm_mhz") or (line.get("clocks") or {}).get("sm_max_mhz")
-            nsm = torch.cuda.get_device_properties(local).multi_processor_count
+            nsm = torch.cuda.get_device_properties(dev).multi_processor_count
             if mhz:
                 smem_frac = wf / (nsm * mhz * 1e6 * ms_o * 1e-3)
         entry = {"value": n / (t_o * 1e-3), "unit": "DOF/s", "ms_per_step": t_o, "iterations": itm,
