@@ -292,6 +292,8 @@ struct ApplyShape {
   // P = 16 kernel (320 threads), whose double-float form would otherwise take 114
   // registers and run one CTA per SM
   static constexpr int MINB8 = (DIM == 3 && NP == 17) ? 2 : 0;
+  // fp32 P = 16: four CTAs per SM (51 registers) to hide the neighbour-line loads
+  static constexpr int MINB4 = (DIM == 3 && NP == 17) ? 4 : 0;
 };
 
 // T: arithmetic and table type; TIO: type of u, f, v in global memory.
@@ -299,7 +301,8 @@ struct ApplyShape {
 // fc = (J (x) J (x) J)^T (f - A u) element by element (Sec. 3.2; J folded as in
 // FoldedJ), in the operation order of the separate restriction kernel.
 template <typename T, int DIM, int NP, bool RESIDUAL, typename TIO = T, int NPC = 0>
-__global__ void __launch_bounds__(ApplyShape<DIM, NP>::THREADS, sizeof(T) == 8 ? ApplyShape<DIM, NP>::MINB8 : 0)
+__global__ void __launch_bounds__(ApplyShape<DIM, NP>::THREADS,
+                                  sizeof(T) == 8 ? ApplyShape<DIM, NP>::MINB8 : ApplyShape<DIM, NP>::MINB4)
 apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const TIO* __restrict__ f,
              TIO* __restrict__ v, FoldedJ<T, NP, NPC> J = FoldedJ<T, NP, NPC>{}, TIO* __restrict__ fc = nullptr) {
   static_assert(NPC == 0 || (RESIDUAL && NPC < NP), "fused restriction: residual, coarser order");
