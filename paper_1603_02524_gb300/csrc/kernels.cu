@@ -96,6 +96,12 @@ transfer_kernel(long long nelem, FoldedJ<T, NPF, NPC> J, const T* __restrict__ i
   T* b1 = b0 + NIN * NIN * NZI;
   T* b2 = b1 + NOUT * NIN * NZI;
   const long long e = blockIdx.x;
+  // FP64: the coefficients from a shared-memory copy (as constant operands the
+  // compiler keeps all of them in registers, 130 per thread, one CTA per SM)
+  __shared__ FoldedJ<T, NPF, NPC> sJ;
+  if constexpr (sizeof(T) == 8) {
+    if (threadIdx.x == 0) sJ = J;
+  }
   for (int t = threadIdx.x; t < NIN * NIN * NZI; t += blockDim.x)
     b0[t] = in[e * (NIN * NIN * NZI) + t];
   __syncthreads();
@@ -105,8 +111,13 @@ transfer_kernel(long long nelem, FoldedJ<T, NPF, NPC> J, const T* __restrict__ i
     T x[NIN];
 #pragma unroll
     for (int a = 0; a < NIN; ++a) x[a] = src[a * sstride];
-    if constexpr (PROLONG) fold_prolong<T, NPF, NPC>(J, x, put);
-    else fold_restrict<T, NPF, NPC>(J, x, put);
+    const FoldedJ<T, NPF, NPC>* jp = &J;
+    if constexpr (sizeof(T) == 8) {
+      jp = &sJ;
+      asm volatile("" : "+l"(jp));             // opaque per line: loaded as used, not hoisted
+    }
+    if constexpr (PROLONG) fold_prolong<T, NPF, NPC>(*jp, x, put);
+    else fold_restrict<T, NPF, NPC>(*jp, x, put);
   };
 #pragma unroll 1
   for (int r = threadIdx.x; r < NIN * NZI; r += blockDim.x) {          // x: lines (y, z)
