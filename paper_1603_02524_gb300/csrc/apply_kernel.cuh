@@ -304,7 +304,8 @@ template <typename T, int DIM, int NP, bool RESIDUAL, typename TIO = T, int NPC 
 __global__ void __launch_bounds__(ApplyShape<DIM, NP>::THREADS,
                                   sizeof(T) == 8 ? ApplyShape<DIM, NP>::MINB8 : ApplyShape<DIM, NP>::MINB4)
 apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const TIO* __restrict__ f,
-             TIO* __restrict__ v, FoldedJ<T, NP, NPC> J = FoldedJ<T, NP, NPC>{}, TIO* __restrict__ fc = nullptr) {
+             TIO* __restrict__ v, FoldedJ<T, NP, NPC> J = FoldedJ<T, NP, NPC>{}, TIO* __restrict__ fc = nullptr,
+             const int* __restrict__ unz = nullptr) {
   static_assert(NPC == 0 || (RESIDUAL && NPC < NP), "fused restriction: residual, coarser order");
   using S = ApplyShape<DIM, NP>;
   constexpr int P = NP - 1;
@@ -315,6 +316,16 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
   const long long e0 = (long long)blockIdx.x * S::EPB;
   const long long nodes_blk = (long long)S::EPB * S::NODES;
   const long long total = dm.nelem * S::NODES;
+  if constexpr (NPC == 0) {
+    // u identically zero (flag from any_nonzero_kernel): A u = 0, so v = f (or 0)
+    if (unz && __ldg(unz) == 0) {
+      for (int t = tid; t < nodes_blk; t += blockDim.x) {
+        const long long g = e0 * S::NODES + t;
+        if (g < total) v[g] = RESIDUAL ? f[g] : TIO(0);
+      }
+      return;
+    }
+  }
   // element coordinates of the block's elements (one 64-bit division set per element)
   __shared__ int s_me[S::EPB][3];
   if (tid < S::EPB) {
@@ -504,16 +515,20 @@ static int apply_dispatch_axes(const LevelDims& dm, const ApplyTables<T>& at, co
 
 template <typename T, int DIM, int NP, typename TIO = T>
 static int apply_dispatch(const LevelDims& dm, const ApplyTables<T>& at, const TIO* u, const TIO* f,
-                          TIO* v, cudaStream_t s) {
+                          TIO* v, cudaStream_t s, const int* unz = nullptr) {
   using S = ApplyShape<DIM, NP>;
   long long blocks = (dm.nelem + S::EPB - 1) / S::EPB;
   const size_t smem = 2 * sizeof(T) * S::EPB * S::NODES;
   if (f) {
     if (!set_smem(apply_kernel<T, DIM, NP, true, TIO>, smem)) return PMG_ECUDA;
-    count_launch(); apply_kernel<T, DIM, NP, true, TIO><<<(unsigned)blocks, S::THREADS, smem, s>>>(dm, at, u, f, v);
+    count_launch();
+    apply_kernel<T, DIM, NP, true, TIO><<<(unsigned)blocks, S::THREADS, smem, s>>>(
+        dm, at, u, f, v, FoldedJ<T, NP, 0>{}, nullptr, unz);
   } else {
     if (!set_smem(apply_kernel<T, DIM, NP, false, TIO>, smem)) return PMG_ECUDA;
-    count_launch(); apply_kernel<T, DIM, NP, false, TIO><<<(unsigned)blocks, S::THREADS, smem, s>>>(dm, at, u, f, v);
+    count_launch();
+    apply_kernel<T, DIM, NP, false, TIO><<<(unsigned)blocks, S::THREADS, smem, s>>>(
+        dm, at, u, f, v, FoldedJ<T, NP, 0>{}, nullptr, unz);
   }
   return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
 }

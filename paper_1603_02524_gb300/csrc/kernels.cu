@@ -14,10 +14,10 @@ namespace pmg {
 
 template <typename T>
 int launch_apply(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f, T* v,
-                 cudaStream_t s) {
+                 cudaStream_t s, const int* unz) {
   if (dm.nelem == 0) return PMG_OK;
 #define PMG_APPLY_CASE(DIMV, NPV) \
-  if (dm.dim == DIMV && dm.NP == NPV) return apply_dispatch<T, DIMV, NPV>(dm, at, u, f, v, s);
+  if (dm.dim == DIMV && dm.NP == NPV) return apply_dispatch<T, DIMV, NPV>(dm, at, u, f, v, s, unz);
   PMG_APPLY_CASE(3, 2) PMG_APPLY_CASE(3, 3) PMG_APPLY_CASE(3, 5) PMG_APPLY_CASE(3, 9)
   PMG_APPLY_CASE(3, 17)
   if (dm.dim == 3 && dm.NP == 33) return apply_dispatch_axes<T, 33, T>(dm, at, u, f, v, s);
@@ -47,9 +47,23 @@ template int launch_residual_restrict<float>(const LevelDims&, const ApplyTables
                                              const float*, const float*, const double*, float*, cudaStream_t);
 
 template int launch_apply<double>(const LevelDims&, const ApplyTables<double>&, const double*,
-                                  const double*, double*, cudaStream_t);
+                                  const double*, double*, cudaStream_t, const int*);
 template int launch_apply<float>(const LevelDims&, const ApplyTables<float>&, const float*,
-                                 const float*, float*, cudaStream_t);
+                                 const float*, float*, cudaStream_t, const int*);
+
+// *flag = 1 if some x[i] != 0 (a NaN counts as nonzero); the caller zeroes the flag
+__global__ void __launch_bounds__(256) any_nonzero_kernel(const double* __restrict__ x, long long n, int* flag) {
+  bool nz = false;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) nz |= !(x[i] == 0.0);
+  if (__syncthreads_or(nz) && threadIdx.x == 0) *flag = 1;
+}
+void launch_any_nonzero(const double* x, long long n, int* flag, cudaStream_t s) {
+  if (n <= 0) return;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  count_launch();
+  any_nonzero_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, n, flag);
+}
 
 // ---------------------------------------------------------------------------
 // g = M f: diagonal GLL mass (Sec. 2.4 right-hand side)

@@ -239,6 +239,7 @@ struct Hier {
   double* partial = nullptr;       // reduction partials
   unsigned* counter = nullptr;     // last-block counter
   int* dstatus = nullptr;          // device status word
+  int* duz = nullptr;              // 1 if the solve's initial u has a nonzero entry
   double* hscal = nullptr;         // pinned host mirror (host_mirror_bytes): control words, results
   double *g_host_stage = nullptr, *u_host_stage = nullptr;   // device buffers for solve_host
   std::vector<void*> owned;
@@ -308,9 +309,11 @@ void stack_tables(const AxisTables& t, int k, int skip, AxisTables& out);
 // ----------------------------------------------------------------------------
 // kernels (launch wrappers)
 // ----------------------------------------------------------------------------
+// unz (optional): a device word, 0 if u is identically zero (any_nonzero found no
+// nonzero entry); the kernel then forms v = f (or 0) without the apply
 template <typename T>
 int launch_apply(const LevelDims& dm, const ApplyTables<T>& at, const T* u, const T* f, T* v,
-                 cudaStream_t s);
+                 cudaStream_t s, const int* unz = nullptr);
 // Transfers: J the device copy of J_l (used where the kernels contract densely,
 // 3-D P = 32 <-> 16), Jh the host copy (fine x coarse, row-major), folded into the
 // kernel parameters of the others.
@@ -325,8 +328,10 @@ int launch_restrict(const LevelDims& fine, const LevelDims& coarse, const T* J, 
 template <typename T>
 int launch_prolong(const LevelDims& fine, const LevelDims& coarse, const T* J, const double* Jh,
                    const T* uc, T* uf, cudaStream_t s);
+// *flag = 1 if x[0..n) has an entry != 0 (flag zeroed by the caller)
+void launch_any_nonzero(const double* x, long long n, int* flag, cudaStream_t s);
 int launch_apply_df(const LevelDims& dm, const ApplyTables<dfloat>& at, const double* u,
-                    const double* f, double* v, cudaStream_t s);
+                    const double* f, double* v, cudaStream_t s, const int* unz = nullptr);
 int launch_coarse_fdm(const LevelDims& dm, const CoarseFdm& c, const double* f, double* u,
                       cudaStream_t s, bool cooperative = true);
 template <typename Ta, typename Tb>

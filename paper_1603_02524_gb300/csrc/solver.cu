@@ -490,12 +490,13 @@ void precondition_graph(Hier& h, cudaStream_t s) {
 
 // The outer CG's operator apply on the finest level: v = A u, or v = f - A u
 // (f non-null); FP64, or double-float on the FP32 pipes (outer_apply option).
-void outer_apply(Hier& h, const double* u, const double* f, double* v, cudaStream_t s) {
+void outer_apply(Hier& h, const double* u, const double* f, double* v, cudaStream_t s,
+                 const int* unz = nullptr) {
   const LevelDims& dm = h.dims[h.L];
   if (h.opt.outer_apply == PMG_OUTER_DF) {
-    PMG_CHECK(launch_apply_df(dm, h.at_df, u, f, v, s));
+    PMG_CHECK(launch_apply_df(dm, h.at_df, u, f, v, s, unz));
   } else {
-    PMG_CHECK(launch_apply<double>(dm, h.d64[h.L].at, u, f, v, s));
+    PMG_CHECK(launch_apply<double>(dm, h.d64[h.L].at, u, f, v, s, unz));
   }
 }
 // Algorithm 2 in three pieces shared by the host-driven solve and the captured one, for
@@ -513,7 +514,11 @@ void cg_begin(Hier& h, const double* g, double* u, const cudaGraphConditionalHan
   const long long n = h.n1;
   const int k = h.nrhs, nb = reduce_blocks(n);
   PMG_CUDA(cudaMemsetAsync(h.dstatus, 0, (kCtrlSeg + 4 * k) * sizeof(int), s));
-  outer_apply(h, u, g, h.r, s);
+  // r = g - A u; from a zero initial guess (checked on the device, so that a captured
+  // solve keeps the test) the apply kernel forms r = g without the apply
+  PMG_CUDA(cudaMemsetAsync(h.duz, 0, sizeof(int), s));
+  launch_any_nonzero(u, n * k, h.duz, s);
+  outer_apply(h, u, g, h.r, s, h.duz);
   if (h.dims[h.L].periodic) launch_sub_mean(h.r, n, h.partial, h.counter, h.scal, nb, s);   // nrhs = 1
   launch_dot(h.r, h.r, nullptr, n, k, h.partial, h.counter, h.scal + S_RR0, nb, s);
   PMG_CUDA(cudaMemsetAsync(h.r_old, 0, (size_t)k * n * sizeof(double), s));
@@ -1041,6 +1046,7 @@ int pmg_hierarchy_build(pmg_grid g, const pmg_options* opt, pmg_hier* out) {
     h->partial = dev_alloc<double>(h->owned, (size_t)kPartialStride * k);
     h->counter = dev_alloc<unsigned>(h->owned, k);
     h->dstatus = dev_alloc<int>(h->owned, kCtrlSeg + 4 * k);
+    h->duz = dev_alloc<int>(h->owned, 1);
     h->hist = dev_alloc<double>(h->owned, (size_t)(o.max_iter + 1) * k);
     h->dres = dev_alloc<SolveResult>(h->owned, k);
     PMG_CUDA(cudaMemset(h->counter, 0, k * sizeof(unsigned)));

@@ -198,6 +198,36 @@ def test_mgcg_solve(case, kind):
     assert rel_err(got, ref) < 1e-10
 
 
+@pytest.mark.parametrize("outer", ["fp64", "df"])
+@pytest.mark.parametrize("case", [CASES[0], CASES[3]], ids=[IDS[0], IDS[3]])
+def test_mgcg_solve_from_nonzero_initial_guess(case, outer):
+    """Algorithm 2 from a seeded nonzero u_0: the initial residual g - A u_0 is formed by the
+    operator apply (a zero u_0 takes the shortcut r_0 = g), in the host-driven loop and in
+    the device-side loop, against the oracle's solve from the same u_0."""
+    dim, P, ne, sp, per, beta = case
+    g, h = make(case, smoother="EA", outer_apply=outer)
+    oh = OHier(dim, P, sp, per, beta, smoother="EA")
+    shape = elem_shape(dim, ne, P)
+    F = e2g(rnd(shape, 13), dim)
+    U0 = e2g(rnd(shape, 14), dim)
+    if per:
+        F -= F.mean()
+    U, ohist = mgcg(oh, U0.copy(), F, rtol=1e-10)
+    ref = g2e(U, ne, P)
+    for run in range(2):                          # host-driven loop, then the device loop
+        u = to_dev(g2e(U0, ne, P))
+        rc, iters, hist = h.solve(to_dev(g2e(F, ne, P)), u, rtol=1e-10)
+        assert rc == 0 and h.last_device_loop == (run == 1)
+        assert iters == len(ohist) - 1
+        assert np.allclose(hist, ohist, rtol=1e-6, atol=1e-12 * ohist[0])
+        got = from_dev(u, shape)
+        if per:
+            got, ref2 = got - got.mean(), ref - ref.mean()
+        else:
+            ref2 = ref
+        assert rel_err(got, ref2) < 1e-10
+
+
 def test_config1_manufactured_solution():
     """2-D unit square, 4x4 elements, P=4, IP, Dirichlet, f = 2 pi^2 sin sin: solve, compare."""
     from paper_1603_02524_gb300 import Grid, Hierarchy
