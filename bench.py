@@ -413,6 +413,7 @@ def main_batch(args):
                        "outer_apply": args.outer_apply, "rtol": 1e-10,
                        "iterations_min_median_max": [min(its), int(statistics.median(its)), max(its)],
                        "l2": "flushed between steps (256 MB write); 4 GB of vectors", "one_graph_launch": True,
+                       "initial_guess": "zero (checked on the device each solve)",
                        "setup_s": t_setup, "autotune_s": t_tune, "capture_s": t_capture,
                        "parallelism": f"replicas{world}"},
             "gpu_launches": int(launches), "clocks": clk}
@@ -570,6 +571,8 @@ def main():
                        "precision": args.precision, "outer_apply": args.outer_apply, "autotune": args.autotune,
                        "smoother": opts["smoother"] + "_l", "flux": "IP" if w.beta == 0 else "LDG",
                        "rtol": 1e-10, "iterations": iters[0], "l2": "flushed between steps (256 MB write)",
+                       "initial_guess": "zero (the solve checks u_0 on the device each step and forms r_0 = g "
+                                        "without the operator apply when it is zero)",
                        "parallelism": f"replicas{world}"},
             "gpu_launches": int(launches), "clocks": clk}
 
