@@ -24,6 +24,10 @@
 //   pass 3  backward c  m = b' + NBP a',  k = c'
 //   pass 4  backward b  m = a' + NAP c,   k = b'
 //   pass 5  backward a  m = b + NBP c,    k = a'
+// For patches whose padded extents are all 24 (PERM: 17 to 23 nodes per axis) the
+// line indices c of A1, a' of A2/A3 (and of A4, composed) and c of A5 are permuted
+// within blocks of 8 (tc_sig, tc_tau), so that the two patch lines a 32-row warp
+// covers store into disjoint shared-memory banks.
 // With the padded strides, the shared-memory offset of output j of a row is the
 // thread's base offset plus a compile-time step.  Each pass's read-back writes,
 // for a fixed output, consecutive K indices from consecutive threads (except
@@ -54,17 +58,24 @@ struct TcGeom {
   // fastest row index of every operand padded to a multiple of 8, so that a row
   // step of the slow index is a whole number of 8-row core-matrix groups
   static constexpr int NAP = (NA + 7) / 8 * 8, NBP = (NB + 7) / 8 * 8, NCP = (NC + 7) / 8 * 8;
-  static constexpr int M0 = NBP * NC;   // passes 0, 5: rows b + NBP c
-  static constexpr int M1 = NCP * NA;   // pass 1:      rows c + NCP a'
-  static constexpr int M2 = NBP * NA;   // passes 2, 3: rows b + NBP a'
-  static constexpr int M4 = NAP * NC;   // pass 4:      rows a' + NAP c
+  // Row permutations (PERM, all extents padded to 24): a warp's 32 rows span two
+  // patch lines, whose read-back stores would share banks in the next operand; the
+  // next operand's rows are permuted (tc_sig, tc_tau below) so that the second line
+  // lands on the banks the first leaves free.
+  static constexpr bool PERM = NAP == 24 && NBP == 24 && NCP == 24;
+  static constexpr int M0 = NBP * NC;   // pass 0:      rows b + NBP c
+  static constexpr int M5 = PERM ? NBP * NCP : NBP * NC;   // pass 5: rows b + NBP tau(c)
+  static constexpr int M1 = NCP * NA;   // pass 1:      rows sig(c) + NCP a'
+  static constexpr int M2 = PERM ? NBP * NAP : NBP * NA;   // passes 2, 3: rows b + NBP tau(a')
+  static constexpr int M4 = NAP * NC;   // pass 4:      rows sig(tau(a')) + NAP c
   static constexpr uint32_t LBO = 144;                            // A: core matrices along K
   __host__ __device__ static constexpr uint32_t sbo(int n) { return (uint32_t)(kp(n) / 4) * LBO; }
   __host__ __device__ static constexpr uint32_t abytes(int n, int m) { return (uint32_t)mt(m) * 16u * sbo(n); }
   __host__ __device__ static constexpr uint32_t mx(uint32_t x, uint32_t y) { return x > y ? x : y; }
   static constexpr int FS = (NA + 3) / 4 * 4 % 8 == 0 ? (NA + 3) / 4 * 4 + 4 : (NA + 3) / 4 * 4;  // staging row stride
   static constexpr uint32_t ABYTES =
-      (mx(mx(mx(abytes(NA, M0), abytes(NB, M1)), mx(abytes(NC, M2), abytes(NB, M4))), 4u * NB * NC * FS) + 1023) /
+      (mx(mx(mx(mx(abytes(NA, M0), abytes(NA, M5)), abytes(NB, M1)), mx(abytes(NC, M2), abytes(NB, M4))),
+          4u * NB * NC * FS) + 1023) /
       1024 * 1024;
   // B tables: dense K-major (core matrices 128 bytes apart along K)
   __host__ __device__ static constexpr uint32_t tsbo(int n) { return (uint32_t)(kp(n) / 4) * 128u; }
@@ -82,7 +93,8 @@ struct TcGeom {
   static constexpr uint32_t BAR_OFF = (LAM_OFF + 4u * (NA + NB + NC) + 15) / 16 * 16;
   static constexpr uint32_t BYTES = BAR_OFF + 32;
   __host__ __device__ static constexpr uint32_t cols(int n, int m) { return (uint32_t)mt(m) * (uint32_t)npd(n); }
-  static constexpr uint32_t COLS_USED = mx(mx(cols(NA, M0), cols(NB, M1)), mx(cols(NC, M2), cols(NB, M4)));
+  static constexpr uint32_t COLS_USED =
+      mx(mx(mx(cols(NA, M0), cols(NA, M5)), cols(NB, M1)), mx(cols(NC, M2), cols(NB, M4)));
   static constexpr uint32_t TCOLS = COLS_USED <= 32 ? 32 : COLS_USED <= 64 ? 64 : COLS_USED <= 128 ? 128 : 256;
   static_assert(COLS_USED <= 256, "accumulators exceed the tensor-memory budget of one CTA");
   static_assert(NA <= 32 && NB <= 32 && NC <= 32 && NC > 1, "tensor-core patch kernel: 3-D, n <= 32");
@@ -102,6 +114,21 @@ template <int NA, int NB, int NC, int N>
 __device__ __forceinline__ void tc_table_async(float* B, const float* __restrict__ src) {
   for (int i = threadIdx.x; i < N * N; i += blockDim.x) cp_async<4>(B + tc_boff<NA, NB, NC, N>(i), src + i, true);
 }
+// The row permutations of PERM shapes, on [0, 24) and mapping each block of 8 to
+// itself.  tc_sig moves consecutive line indices to rows whose bank offsets differ by
+// 24 words (4 x 6 mod 32) within each block of 4; tc_tau reverses the last three of
+// each block of 4, so that consecutive line indices land 3 rows (24 words mod 32) apart;
+// tc_tau is its own inverse.
+__device__ __forceinline__ int tc_sig(int c) {
+  const int k = c >> 2, q = k & 1, g = k >> 1, i = c & 3;
+  return 8 * g + ((q + 6 * i - 6 * g + 48) & 7);
+}
+__device__ __forceinline__ int tc_sig_inv(int r) {
+  const int g = r >> 3, s = r & 7, q = s & 1;
+  return 4 * (2 * g + q) + ((3 * ((s - q) >> 1) + g) & 3);
+}
+__device__ __forceinline__ int tc_tau(int a) { return (a & ~3) | ((3 * (a & 3)) & 3); }
+
 // Store accumulator row m (registers r, outputs j = 0..) of pass PASS as the next
 // pass's operand (or, after the last pass, into the staging rows); rows beyond the
 // patch extents are padding and are dropped.
@@ -112,23 +139,24 @@ __device__ __forceinline__ void tc_store_row(float* A, int m, const uint32_t (&r
   auto d = [&](int j) { return __uint_as_float(r[j]); };
   // offsets of the next operand: a thread-dependent base plus, for output j, a
   // compile-time step (rows a multiple of 8 apart, or a fixed position in K)
-  if constexpr (PASS == 0) {                   // m = b + NBP c -> A1[c + NCP a'][b]
+  if constexpr (PASS == 0) {                   // m = b + NBP c -> A1[sig(c) + NCP a'][b]
     constexpr int S = (int)G::sbo(NB) / 4;
     const int b = m % G::NBP, c = m / G::NBP;
     if (b >= NB || c >= NC) return;
-    const int base = (c >> 3) * S + (c & 7) * 4 + (b >> 2) * 36 + (b & 3);
+    const int cr = G::PERM ? tc_sig(c) : c;
+    const int base = (cr >> 3) * S + (cr & 7) * 4 + (b >> 2) * 36 + (b & 3);
 #pragma unroll
     for (int j = 0; j < NA; ++j) A[base + j * (G::NCP / 8) * S] = d(j);
-  } else if constexpr (PASS == 1) {            // m = c + NCP a' -> A2[b' + NBP a'][c]
+  } else if constexpr (PASS == 1) {            // m = sig(c) + NCP a' -> A2[b' + NBP tau(a')][c]
     constexpr int S = (int)G::sbo(NC) / 4;
-    const int c = m % G::NCP, a = m / G::NCP;
+    const int c = G::PERM ? tc_sig_inv(m % G::NCP) : m % G::NCP, a = m / G::NCP;
     if (c >= NC || a >= NA) return;
-    const int base = a * (G::NBP / 8) * S + (c >> 2) * 36 + (c & 3);
+    const int base = (G::PERM ? tc_tau(a) : a) * (G::NBP / 8) * S + (c >> 2) * 36 + (c & 3);
 #pragma unroll
     for (int j = 0; j < NB; ++j) A[base + (j >> 3) * S + (j & 7) * 4] = d(j);
-  } else if constexpr (PASS == 2) {            // m = b' + NBP a' -> A3[m][c'] / (la + lb + lc)
+  } else if constexpr (PASS == 2) {            // m = b' + NBP tau(a') -> A3[m][c'] / (la + lb + lc)
     constexpr int S = (int)G::sbo(NC) / 4;
-    const int b = m % G::NBP, a = m / G::NBP;
+    const int b = m % G::NBP, a = G::PERM ? tc_tau(m / G::NBP) : m / G::NBP;
     if (b >= NB || a >= NA) return;
     const float s0 = la[a] + lb[b];
     float4* dst = reinterpret_cast<float4*>(A + (m >> 3) * S + (m & 7) * 4);   // 4 K values: 16 bytes
@@ -139,22 +167,23 @@ __device__ __forceinline__ void tc_store_row(float* A, int m, const uint32_t (&r
       for (int k = 0; k < 4; ++k) v[k] = (4 * g + k < NC) ? d(4 * g + k) * recip(s0 + lc[4 * g + k]) : 0.0f;
       dst[g * 9] = make_float4(v[0], v[1], v[2], v[3]);                        // groups 144 bytes apart
     }
-  } else if constexpr (PASS == 3) {            // m = b' + NBP a' -> A4[a' + NAP c][b']
+  } else if constexpr (PASS == 3) {            // m = b' + NBP tau(a') -> A4[sig(tau(a')) + NAP c][b']
     constexpr int S = (int)G::sbo(NB) / 4;
-    const int b = m % G::NBP, a = m / G::NBP;
+    const int b = m % G::NBP, u = m / G::NBP, a = G::PERM ? tc_tau(u) : u;
     if (b >= NB || a >= NA) return;
-    const int base = (a >> 3) * S + (a & 7) * 4 + (b >> 2) * 36 + (b & 3);
+    const int ar = G::PERM ? tc_sig(u) : a;    // sig(tau(a')) = sig(u)
+    const int base = (ar >> 3) * S + (ar & 7) * 4 + (b >> 2) * 36 + (b & 3);
 #pragma unroll
     for (int j = 0; j < NC; ++j) A[base + j * (G::NAP / 8) * S] = d(j);
-  } else if constexpr (PASS == 4) {            // m = a' + NAP c -> A5[b + NBP c][a']
+  } else if constexpr (PASS == 4) {            // m = sig(tau(a')) + NAP c -> A5[b + NBP tau(c)][a']
     constexpr int S = (int)G::sbo(NA) / 4;
-    const int a = m % G::NAP, c = m / G::NAP;
+    const int a = G::PERM ? tc_tau(tc_sig_inv(m % G::NAP)) : m % G::NAP, c = m / G::NAP;
     if (a >= NA || c >= NC) return;
-    const int base = c * (G::NBP / 8) * S + (a >> 2) * 36 + (a & 3);
+    const int base = (G::PERM ? tc_tau(c) : c) * (G::NBP / 8) * S + (a >> 2) * 36 + (a & 3);
 #pragma unroll
     for (int j = 0; j < NB; ++j) A[base + (j >> 3) * S + (j & 7) * 4] = d(j);
-  } else {                                     // m = b + NBP c -> staging row b + NB c
-    const int b = m % G::NBP, c = m / G::NBP;
+  } else {                                     // m = b + NBP tau(c) -> staging row b + NB c
+    const int b = m % G::NBP, c = G::PERM ? tc_tau(m / G::NBP) : m / G::NBP;
     if (b >= NB || c >= NC) return;
     float4* st = reinterpret_cast<float4*>(A + (b + NB * c) * G::FS);
 #pragma unroll
@@ -175,7 +204,7 @@ __device__ __forceinline__ bool tc_pass(float* A, const float* B, uint64_t* mbar
   using G = TcGeom<NA, NB, NC>;
   constexpr int q = (PASS == 0 || PASS == 5) ? 0 : (PASS == 1 || PASS == 4) ? 1 : 2;
   constexpr int n = q == 0 ? NA : q == 1 ? NB : NC;
-  constexpr int M = (PASS == 0 || PASS == 5) ? G::M0 : PASS == 1 ? G::M1 : PASS == 4 ? G::M4 : G::M2;
+  constexpr int M = PASS == 0 ? G::M0 : PASS == 5 ? G::M5 : PASS == 1 ? G::M1 : PASS == 4 ? G::M4 : G::M2;
   constexpr int KS = G::kp(n) / 8, NPD = G::npd(n), MT = G::mt(M);
   constexpr uint32_t SB = G::sbo(n);
   constexpr uint32_t idesc = umma::idesc_tf32(128, NPD);
