@@ -68,7 +68,7 @@ TRAFFIC_PER_PATCH = {
 # is bound by.  Key: (P, family).  Utilisation = wavefronts / (SMs x SM clock x sweep
 # time) at one wavefront per SM and cycle.
 TC_SMEM_WAVEFRONTS_PER_PATCH = {
-    (16, "EA"): (38481661 + 14745600) / 4096,
+    (16, "EA"): (32083706 + 14745600) / 4096,
 }
 
 
