@@ -120,3 +120,22 @@ def test_p32_mgcg(case):
         got = got - got.mean()
         ref = ref - ref.mean()
     assert rel_err(got, ref) < 1e-9
+
+
+@pytest.mark.parametrize("kind", ["EA", "FA"])
+def test_p32_mgcg_autotuned(kind):
+    """The tuner times both forms of the large-patch kernel per family (scratch buffer, or
+    slabs of c-planes in shared memory) and keeps the faster: FP64 solves with its choice
+    against the oracle (iteration count, solution to 1e-10)."""
+    case = CASES[0]
+    dim, P, ne, sp, per, beta = case
+    g, h = make(case, smoother=kind)
+    h.autotune()
+    shape = elem_shape(dim, ne, P)
+    F = e2g(rnd(shape, 41), dim)
+    oh = OHier(dim, P, sp, per, beta, smoother=kind)
+    U, ohist = mgcg(oh, np.zeros_like(F), F, rtol=1e-10)
+    u = torch.zeros(int(np.prod(shape)), dtype=torch.float64, device="cuda")
+    rc, it, _ = h.solve(to_dev(g2e(F, ne, P)), u, rtol=1e-10)
+    assert rc == 0 and it == len(ohist) - 1
+    assert rel_err(from_dev(u, shape), g2e(U, ne, P)) < 1e-10
