@@ -235,7 +235,8 @@ int pmg_vcycle(pmg_hier h, const double* f_dev, double* u_dev, void* stream);
 /*
  * Inexact multigrid-preconditioned CG (Algorithm 2; beta by Golub-Ye,
  * z^T (r - r_old) / delta).  g_dev: right-hand side (periodic grids: projected
- * onto zero mean internally).  u_dev: initial guess in, solution out.
+ * onto zero mean internally).  u_dev: initial guess in, solution out; the solve checks on
+ * the device whether the guess is all zero and then takes r_0 = g without an operator apply.
  * Stops when ||r||_2 <= rtol * ||r_0||_2 or after opt.max_iter iterations
  * (PMG_ENOCONV, u holds the last iterate).  stats may be NULL.  A hierarchy with
  * nrhs > 1 solves its nrhs right-hand sides (g_dev, u_dev: nrhs vectors back to back),
