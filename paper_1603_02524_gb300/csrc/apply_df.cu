@@ -13,7 +13,7 @@ int launch_apply_df(const LevelDims& dm, const ApplyTables<dfloat>& at, const do
   if (dm.dim == DIMV && dm.NP == NPV) return apply_dispatch<dfloat, DIMV, NPV, double>(dm, at, u, f, v, s, unz);
   PMG_APPLY_CASE(3, 2) PMG_APPLY_CASE(3, 3) PMG_APPLY_CASE(3, 5) PMG_APPLY_CASE(3, 9)
   PMG_APPLY_CASE(3, 17)
-  if (dm.dim == 3 && dm.NP == 33) return apply_dispatch_axes<dfloat, 33, double>(dm, at, u, f, v, s);
+  if (dm.dim == 3 && dm.NP == 33) return apply_dispatch_axes<dfloat, 33, double>(dm, at, u, f, v, s, unz);
   PMG_APPLY_CASE(2, 2) PMG_APPLY_CASE(2, 3) PMG_APPLY_CASE(2, 5) PMG_APPLY_CASE(2, 9)
   PMG_APPLY_CASE(2, 17) PMG_APPLY_CASE(2, 33)
 #undef PMG_APPLY_CASE

@@ -463,12 +463,23 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
 template <typename T, int NP, bool RESIDUAL, typename TIO>
 __global__ void __launch_bounds__(128)
 apply_axis_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u,
-                  const TIO* __restrict__ f, TIO* __restrict__ v, int d) {
+                  const TIO* __restrict__ f, TIO* __restrict__ v, int d, const int* __restrict__ unz) {
   constexpr int LINES = NP * NP, NODES = NP * NP * NP;
   const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (gid >= dm.nelem * LINES) return;
   const long long e = gid / LINES;
   const int line = (int)(gid - e * LINES);
+  if (unz && __ldg(unz) == 0) {
+    // u identically zero: v = f (or 0), written by the last axis's launch, line by line
+    if (d == 2) {
+#pragma unroll 1
+      for (int i = 0; i < NP; ++i) {
+        const long long g = e * NODES + line + (long long)i * NP * NP;
+        v[g] = RESIDUAL ? f[g] : TIO(0);
+      }
+    }
+    return;
+  }
   const int me[3] = {(int)(e % dm.ne[0]), (int)((e / dm.ne[0]) % dm.ne[1]),
                      (int)(e / ((long long)dm.ne[0] * dm.ne[1]))};
   int off, stride;
@@ -502,13 +513,13 @@ apply_axis_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u,
 
 template <typename T, int NP, typename TIO>
 static int apply_dispatch_axes(const LevelDims& dm, const ApplyTables<T>& at, const TIO* u, const TIO* f,
-                               TIO* v, cudaStream_t s) {
+                               TIO* v, cudaStream_t s, const int* unz = nullptr) {
   const long long threads = dm.nelem * NP * NP;
   const long long blocks = (threads + 127) / 128;
   for (int d = 0; d < 3; ++d) {
     count_launch();
-    if (f) apply_axis_kernel<T, NP, true, TIO><<<(unsigned)blocks, 128, 0, s>>>(dm, at, u, f, v, d);
-    else apply_axis_kernel<T, NP, false, TIO><<<(unsigned)blocks, 128, 0, s>>>(dm, at, u, f, v, d);
+    if (f) apply_axis_kernel<T, NP, true, TIO><<<(unsigned)blocks, 128, 0, s>>>(dm, at, u, f, v, d, unz);
+    else apply_axis_kernel<T, NP, false, TIO><<<(unsigned)blocks, 128, 0, s>>>(dm, at, u, f, v, d, unz);
   }
   return cudaGetLastError() == cudaSuccess ? PMG_OK : PMG_ECUDA;
 }

@@ -20,7 +20,7 @@ int launch_apply(const LevelDims& dm, const ApplyTables<T>& at, const T* u, cons
   if (dm.dim == DIMV && dm.NP == NPV) return apply_dispatch<T, DIMV, NPV>(dm, at, u, f, v, s, unz);
   PMG_APPLY_CASE(3, 2) PMG_APPLY_CASE(3, 3) PMG_APPLY_CASE(3, 5) PMG_APPLY_CASE(3, 9)
   PMG_APPLY_CASE(3, 17)
-  if (dm.dim == 3 && dm.NP == 33) return apply_dispatch_axes<T, 33, T>(dm, at, u, f, v, s);
+  if (dm.dim == 3 && dm.NP == 33) return apply_dispatch_axes<T, 33, T>(dm, at, u, f, v, s, unz);
   PMG_APPLY_CASE(2, 2) PMG_APPLY_CASE(2, 3) PMG_APPLY_CASE(2, 5) PMG_APPLY_CASE(2, 9)
   PMG_APPLY_CASE(2, 17) PMG_APPLY_CASE(2, 33)
 #undef PMG_APPLY_CASE
