@@ -461,7 +461,8 @@ apply_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u, const T
 // order, as the staged kernel's accumulator); the launch of the last axis applies
 // the masses and forms v = A u or f - A u.
 template <typename T, int NP, bool RESIDUAL, typename TIO>
-__global__ void __launch_bounds__(128, 3)   // 3 CTAs per SM: the double-float line needs 214 registers uncapped
+// CTAs per SM: fp32 5 (96 registers), 8-byte types 3 (the double-float line needs 214 registers uncapped)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 3)
 apply_axis_kernel(LevelDims dm, ApplyTables<T> at, const TIO* __restrict__ u,
                   const TIO* __restrict__ f, TIO* __restrict__ v, int d, const int* __restrict__ unz) {
   constexpr int LINES = NP * NP, NODES = NP * NP * NP;
