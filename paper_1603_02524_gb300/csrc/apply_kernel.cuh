@@ -199,86 +199,187 @@ __device__ __forceinline__ void apply_line(const ApplyTables<T>& at, const Apply
   constexpr int P = NP - 1;
   constexpr int H = NP / 2, NE = NP - H, NO = H;
   constexpr int PNP = apad<T>(NP);
-  const T* L0 = ax.L0 + (size_t)ax.m * NP * PNP;
-  if (__ldg(ax.sym + ax.m)) {
-    // even-odd split of the centro-symmetric block (folded, transposed rows)
-    constexpr int PE = apad<T>(NE), PO = apad<T>(NO > 0 ? NO : 1);
-    T xp[NE], xm[NO > 0 ? NO : 1];
-#pragma unroll
-    for (int a = 0; a < H; ++a) {
-      xp[a] = x[a] + x[P - a];
-      xm[a] = x[a] - x[P - a];
-    }
-    if (NE > H) xp[NE - 1] = x[H];
-    T ae[NE], ao[NO > 0 ? NO : 1];
-#pragma unroll
-    for (int i = 0; i < NE; ++i) ae[i] = T(0);
-#pragma unroll
-    for (int i = 0; i < NO; ++i) ao[i] = T(0);
-#pragma unroll
-    for (int a = 0; a < NE; ++a) apply_axpy<T, NE>(ae, L0 + a * PE, xp[a]);
-    if constexpr (NO > 0) {
-#pragma unroll
-      for (int a = 0; a < NO; ++a)
-        apply_axpy<T, NO>(reinterpret_cast<T(&)[NO]>(ao), L0 + NE * PE + a * PO, xm[a]);
-    }
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-      y[i] = ae[i] + ao[i];
-      y[P - i] = ae[i] - ao[i];
-    }
-    if (NE > H) y[H] = ae[H];
-  } else {
-#pragma unroll
-    for (int i = 0; i < NP; ++i) y[i] = T(0);
-#pragma unroll
-    for (int a = 0; a < NP; ++a) apply_axpy<T, NP>(y, L0 + a * PNP, x[a]);
-  }
-  // neighbour blocks L^-, L^+ (rank <= 3, already scaled by M_d^-1)
-  const T* c = ax.cpl + (size_t)ax.m * (2 * PNP + 8);
-  const long long estride = ax.estride;
-  const int ned = ax.ned;
-  // end value and end derivative (row Drow of the differentiation matrix) of the
-  // neighbour line un.  Double-float apply of an FP64 vector: the dot product runs
-  // in FP64 and only its result and the end value are split into two fp32 words
-  // (splitting all NP values and accumulating in double-float took about half of
-  // that kernel's issue slots; the FP64 pipe is otherwise idle there)
-  auto end_terms = [&](const TIO* un, const T* Drow, const double* Drow_d, int iend, T& uend, T& dend) {
-    if constexpr (std::is_same<T, dfloat>::value && std::is_same<TIO, double>::value) {
-      double s = 0.0, v = 0.0;
-#pragma unroll
-      for (int a = 0; a < NP; ++a) {
-        const double val = __ldg(un + a * stride);
-        s = ::fma(__ldg(Drow_d + a), val, s);
-        if (a == iend) v = val;
+  if constexpr (sizeof(T) == 8) {
+    // FP64 and double-float: the neighbour end terms first (their loads in flight during
+    // the element's own block); mirrored coupling rows folded into the even-odd
+    // accumulation (the tables flag them).  fp32 (below) keeps the order of the
+    // contraction first and unfolded tables: holding the end terms across the block
+    // spilled its 48-register budget.
+    const T* L0 = ax.L0 + (size_t)ax.m * NP * PNP;
+    // neighbour blocks L^-, L^+ (rank <= 3, already scaled by M_d^-1)
+    const T* c = ax.cpl + (size_t)ax.m * (2 * PNP + 8);
+    const long long estride = ax.estride;
+    const int ned = ax.ned;
+    // end value and end derivative (row Drow of the differentiation matrix) of the
+    // neighbour line un.  Double-float apply of an FP64 vector: the dot product runs
+    // in FP64 and only its result and the end value are split into two fp32 words
+    // (splitting all NP values and accumulating in double-float took about half of
+    // that kernel's issue slots; the FP64 pipe is otherwise idle there)
+    auto end_terms = [&](const TIO* un, const T* Drow, const double* Drow_d, int iend, T& uend, T& dend) {
+      if constexpr (std::is_same<T, dfloat>::value && std::is_same<TIO, double>::value) {
+        double s = 0.0, v = 0.0;
+  #pragma unroll
+        for (int a = 0; a < NP; ++a) {
+          const double val = __ldg(un + a * stride);
+          s = ::fma(__ldg(Drow_d + a), val, s);
+          if (a == iend) v = val;
+        }
+        uend = T(v);
+        dend = T(s);
+      } else {
+        T s = T(0), v = T(0);
+  #pragma unroll
+        for (int a = 0; a < NP; ++a) {
+          T val = T(__ldg(un + a * stride));
+          s = madd(ldg(Drow + a), val, s);
+          if (a == iend) v = val;
+        }
+        uend = v;
+        dend = s;
       }
-      uend = T(v);
-      dend = T(s);
+    };
+    const bool hasL = ldg(c + 2 * PNP + 2) != T(0), hasR = ldg(c + 2 * PNP + 5) != T(0);
+    T uP = T(0), dP = T(0), u0 = T(0), d0 = T(0);
+
+    {
+      if (hasL) {                                // neighbour m-1
+        const long long en = (ax.m > 0) ? e - estride : e + (long long)(ned - 1) * estride;
+        end_terms(u + en * NODES + off, at.DP, at.DPd, P, uP, dP);
+      }
+      if (hasR) {                                // neighbour m+1
+        const long long en = (ax.m < ned - 1) ? e + estride : e - (long long)(ned - 1) * estride;
+        end_terms(u + en * NODES + off, at.D0, at.D0d, 0, u0, d0);
+      }
+    }
+    // folded coupling (both neighbours, mirrored rows c_R[P - i] = c_L[i]): c_L u_P + c_R u_0
+    // = even part x (u_P + u_0) + odd part x (u_P - u_0)
+    const bool csym = ldg(c + 2 * PNP + 6) != T(0);
+    if (__ldg(ax.sym + ax.m)) {
+      // even-odd split of the centro-symmetric block (folded, transposed rows)
+      constexpr int PE = apad<T>(NE), PO = apad<T>(NO > 0 ? NO : 1);
+      T xp[NE], xm[NO > 0 ? NO : 1];
+  #pragma unroll
+      for (int a = 0; a < H; ++a) {
+        xp[a] = x[a] + x[P - a];
+        xm[a] = x[a] - x[P - a];
+      }
+      if (NE > H) xp[NE - 1] = x[H];
+      T ae[NE], ao[NO > 0 ? NO : 1];
+  #pragma unroll
+      for (int i = 0; i < NE; ++i) ae[i] = T(0);
+  #pragma unroll
+      for (int i = 0; i < NO; ++i) ao[i] = T(0);
+  #pragma unroll
+      for (int a = 0; a < NE; ++a) apply_axpy<T, NE>(ae, L0 + a * PE, xp[a]);
+      if constexpr (NO > 0) {
+  #pragma unroll
+        for (int a = 0; a < NO; ++a)
+          apply_axpy<T, NO>(reinterpret_cast<T(&)[NO]>(ao), L0 + NE * PE + a * PO, xm[a]);
+      }
+      if (csym) {
+        apply_axpy<T, NE>(ae, c, uP + u0);
+        if constexpr (NO > 0) apply_axpy<T, NO>(reinterpret_cast<T(&)[NO]>(ao), c + PNP, uP - u0);
+      }
+  #pragma unroll
+      for (int i = 0; i < H; ++i) {
+        y[i] = ae[i] + ao[i];
+        y[P - i] = ae[i] - ao[i];
+      }
+      if (NE > H) y[H] = ae[H];
     } else {
-      T s = T(0), v = T(0);
-#pragma unroll
-      for (int a = 0; a < NP; ++a) {
-        T val = T(__ldg(un + a * stride));
-        s = madd(ldg(Drow + a), val, s);
-        if (a == iend) v = val;
-      }
-      uend = v;
-      dend = s;
+  #pragma unroll
+      for (int i = 0; i < NP; ++i) y[i] = T(0);
+  #pragma unroll
+      for (int a = 0; a < NP; ++a) apply_axpy<T, NP>(y, L0 + a * PNP, x[a]);
     }
-  };
-  if (ldg(c + 2 * PNP + 2) != T(0)) {          // neighbour m-1 exists
-    long long en = (ax.m > 0) ? e - estride : e + (long long)(ned - 1) * estride;
-    T uP, dP;
-    end_terms(u + en * NODES + off, at.DP, at.DPd, P, uP, dP);
-    apply_axpy<T, NP>(y, c, uP);
-    y[0] += ldg(c + 2 * PNP + 0) * dP - ldg(c + 2 * PNP + 1) * uP;
-  }
-  if (ldg(c + 2 * PNP + 5) != T(0)) {          // neighbour m+1 exists
-    long long en = (ax.m < ned - 1) ? e + estride : e - (long long)(ned - 1) * estride;
-    T u0, d0;
-    end_terms(u + en * NODES + off, at.D0, at.D0d, 0, u0, d0);
-    apply_axpy<T, NP>(y, c + PNP, u0);
-    y[P] = y[P] - (ldg(c + 2 * PNP + 3) * d0 + ldg(c + 2 * PNP + 4) * u0);
+    if (!csym) {
+      if (hasL) apply_axpy<T, NP>(y, c, uP);
+      if (hasR) apply_axpy<T, NP>(y, c + PNP, u0);
+    }
+    if (hasL) y[0] += ldg(c + 2 * PNP + 0) * dP - ldg(c + 2 * PNP + 1) * uP;
+    if (hasR) y[P] = y[P] - (ldg(c + 2 * PNP + 3) * d0 + ldg(c + 2 * PNP + 4) * u0);
+  } else {
+    const T* L0 = ax.L0 + (size_t)ax.m * NP * PNP;
+    if (__ldg(ax.sym + ax.m)) {
+      // even-odd split of the centro-symmetric block (folded, transposed rows)
+      constexpr int PE = apad<T>(NE), PO = apad<T>(NO > 0 ? NO : 1);
+      T xp[NE], xm[NO > 0 ? NO : 1];
+  #pragma unroll
+      for (int a = 0; a < H; ++a) {
+        xp[a] = x[a] + x[P - a];
+        xm[a] = x[a] - x[P - a];
+      }
+      if (NE > H) xp[NE - 1] = x[H];
+      T ae[NE], ao[NO > 0 ? NO : 1];
+  #pragma unroll
+      for (int i = 0; i < NE; ++i) ae[i] = T(0);
+  #pragma unroll
+      for (int i = 0; i < NO; ++i) ao[i] = T(0);
+  #pragma unroll
+      for (int a = 0; a < NE; ++a) apply_axpy<T, NE>(ae, L0 + a * PE, xp[a]);
+      if constexpr (NO > 0) {
+  #pragma unroll
+        for (int a = 0; a < NO; ++a)
+          apply_axpy<T, NO>(reinterpret_cast<T(&)[NO]>(ao), L0 + NE * PE + a * PO, xm[a]);
+      }
+  #pragma unroll
+      for (int i = 0; i < H; ++i) {
+        y[i] = ae[i] + ao[i];
+        y[P - i] = ae[i] - ao[i];
+      }
+      if (NE > H) y[H] = ae[H];
+    } else {
+  #pragma unroll
+      for (int i = 0; i < NP; ++i) y[i] = T(0);
+  #pragma unroll
+      for (int a = 0; a < NP; ++a) apply_axpy<T, NP>(y, L0 + a * PNP, x[a]);
+    }
+    // neighbour blocks L^-, L^+ (rank <= 3, already scaled by M_d^-1)
+    const T* c = ax.cpl + (size_t)ax.m * (2 * PNP + 8);
+    const long long estride = ax.estride;
+    const int ned = ax.ned;
+    // end value and end derivative (row Drow of the differentiation matrix) of the
+    // neighbour line un.  Double-float apply of an FP64 vector: the dot product runs
+    // in FP64 and only its result and the end value are split into two fp32 words
+    // (splitting all NP values and accumulating in double-float took about half of
+    // that kernel's issue slots; the FP64 pipe is otherwise idle there)
+    auto end_terms = [&](const TIO* un, const T* Drow, const double* Drow_d, int iend, T& uend, T& dend) {
+      if constexpr (std::is_same<T, dfloat>::value && std::is_same<TIO, double>::value) {
+        double s = 0.0, v = 0.0;
+  #pragma unroll
+        for (int a = 0; a < NP; ++a) {
+          const double val = __ldg(un + a * stride);
+          s = ::fma(__ldg(Drow_d + a), val, s);
+          if (a == iend) v = val;
+        }
+        uend = T(v);
+        dend = T(s);
+      } else {
+        T s = T(0), v = T(0);
+  #pragma unroll
+        for (int a = 0; a < NP; ++a) {
+          T val = T(__ldg(un + a * stride));
+          s = madd(ldg(Drow + a), val, s);
+          if (a == iend) v = val;
+        }
+        uend = v;
+        dend = s;
+      }
+    };
+    if (ldg(c + 2 * PNP + 2) != T(0)) {          // neighbour m-1 exists
+      long long en = (ax.m > 0) ? e - estride : e + (long long)(ned - 1) * estride;
+      T uP, dP;
+      end_terms(u + en * NODES + off, at.DP, at.DPd, P, uP, dP);
+      apply_axpy<T, NP>(y, c, uP);
+      y[0] += ldg(c + 2 * PNP + 0) * dP - ldg(c + 2 * PNP + 1) * uP;
+    }
+    if (ldg(c + 2 * PNP + 5) != T(0)) {          // neighbour m+1 exists
+      long long en = (ax.m < ned - 1) ? e + estride : e - (long long)(ned - 1) * estride;
+      T u0, d0;
+      end_terms(u + en * NODES + off, at.D0, at.D0d, 0, u0, d0);
+      apply_axpy<T, NP>(y, c + PNP, u0);
+      y[P] = y[P] - (ldg(c + 2 * PNP + 3) * d0 + ldg(c + 2 * PNP + 4) * u0);
+    }
   }
 }
 

@@ -95,7 +95,9 @@ struct ApplyAxisHost {
   std::vector<double> L0, cpl;
   std::vector<int> sym;
 };
-void apply_axis_tables(const Axis1DHost& a, ApplyAxisHost& t);
+// fold_coupling: mirrored neighbour-coupling rows stored folded and flagged (the FP64 and
+// double-float applies use them; the fp32 apply keeps the rows unfolded)
+void apply_axis_tables(const Axis1DHost& a, ApplyAxisHost& t, bool fold_coupling = true);
 // the same tables in the apply kernel's accumulate form, rows padded to W entries
 void apply_rowform(const ApplyAxisHost& t, int NP, int W, std::vector<double>& L0r,
                    std::vector<double>& cplr);

@@ -529,7 +529,7 @@ void global_axis_eig(const Axis1DHost& a, std::vector<double>& S, std::vector<do
 // E[i][H] = Lt[i][H] (middle column, odd NP), rows i < NE; then
 // O[i][a] = (Lt[i][a] - Lt[i][P-a]) / 2, i, a < H.  Coupling row (2 NP + 8):
 // [-aL D0_i / M_i]_i, [aR DP_i / M_i]_i, bL/M_0, cL/M_0, hasL, bR/M_P, cR/M_P, hasR.
-void apply_axis_tables(const Axis1DHost& a, ApplyAxisHost& t) {
+void apply_axis_tables(const Axis1DHost& a, ApplyAxisHost& t, bool fold_coupling) {
   const int NP = a.NP, Ne = a.Ne, P = a.P;
   const int H = NP / 2, NE = NP - H, NO = H;
   t.L0.assign((size_t)Ne * NP * NP, 0.0);
@@ -579,6 +579,23 @@ void apply_axis_tables(const Axis1DHost& a, ApplyAxisHost& t) {
     o[2 * NP + 3] = c[5] / M[P];
     o[2 * NP + 4] = c[6] / M[P];
     o[2 * NP + 5] = c[7];
+    // both neighbours, a centro-symmetric block and mirrored coupling rows (c_R[P - i] =
+    // c_L[i]: equal neighbour widths): the rows are stored folded, the even part of c_L
+    // in o[0..NE), the odd part in o[NP..NP + NO), flagged in o[2 NP + 6], so that the
+    // kernel adds c_L u_P + c_R u_0 inside the even-odd accumulation (half the products)
+    bool csym = fold_coupling && sym && c[3] != 0.0 && c[7] != 0.0;
+    double cbig = 0.0;
+    for (int i = 0; i < NP; ++i) cbig = std::max(cbig, std::fabs(o[i]));
+    for (int i = 0; i < NP && csym; ++i)
+      if (std::fabs(o[NP + (P - i)] - o[i]) > 1e-13 * cbig) csym = false;
+    if (csym) {
+      std::vector<double> cl(o, o + NP);
+      for (int i = 0; i < NE; ++i) o[i] = (i < H) ? 0.5 * (cl[i] + cl[P - i]) : cl[H];
+      for (int i = NE; i < NP; ++i) o[i] = 0.0;
+      for (int i = 0; i < NO; ++i) o[NP + i] = 0.5 * (cl[i] - cl[P - i]);
+      for (int i = NO; i < NP; ++i) o[NP + i] = 0.0;
+    }
+    o[2 * NP + 6] = csym ? 1.0 : 0.0;
   }
 }
 

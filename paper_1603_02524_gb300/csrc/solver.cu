@@ -177,7 +177,7 @@ ApplyTables<T> build_apply_tables(Hier& h, int l, std::vector<void*>& own) {
   for (int d = 0; d < 3; ++d) {
     int dd = d < dm.dim ? d : 0;
     ApplyAxisHost t;
-    apply_axis_tables(ax[dd], t);
+    apply_axis_tables(ax[dd], t, sizeof(T) == 8);
     std::vector<double> L0r, cplr;
     apply_rowform(t, dm.NP, 16 / (int)sizeof(T), L0r, cplr);
     at.L0[d] = dev_upload<T>(own, L0r);
